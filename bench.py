@@ -1,0 +1,403 @@
+#!/usr/bin/env python3
+"""Benchmark of the MIDBF apply on GB300 (one JSON line on stdout).
+
+Workload: the 2D generalized Radon transform of Example 1 (Sec. 4) on the
+n = 256 grid, N = 65,536 points, phase x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
+ID tolerance 1e-6, n0 = 64 (L = 5).  Synthetic inputs (synth.py), seeded.
+
+A step is one pass of the whole hot path over one batch: the forward apply
+g = K f followed by the adjoint apply K^H g, both through all levels (V
+levels, the on-the-fly middle factor, U levels), in the mixed form (complex
+FP32), 1 right-hand side.  value = points*RHS processed per second over all
+ranks (2 N per step per rank).  Extra keys report the plain FP64 form, 64
+right-hand sides, the roofline of the dominant kernel, the end-to-end time
+through the host-buffer C entry point, and the CPU oracle.
+
+Multi-GPU: the apply does not shard across GPUs here (replicas only); with
+torchrun each rank runs its own replica and value sums over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "MIDBF apply points*RHS/s and % roofline at rel-L2<=1e-4, mixed vs plain FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(n):
+    X = synth.uniform_grid(n, 2)
+    W = synth.frequency_grid(n, 2)
+    boxX = (np.zeros(2), 1.0)
+    boxW = (np.full(2, -n / 2), float(n))
+    return X, W, boxX, boxW
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return p.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class OracleSample:
+    """The oracle's apply (its sparse factor product, FP64) on a bounded sample
+    of the plan: every `sample_every`-th block of every stage, forward and
+    adjoint; times scale to the whole plan by the fraction of factor entries
+    sampled."""
+
+    def __init__(self, plan_bytes, sample_every=32):
+        from oracle import midbf as omidbf
+        from oracle import planio
+        fac = planio.read(plan_bytes)
+        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        rng = np.random.default_rng(0)
+        self.parts = []
+        sampled = total = 0
+        in_len = fac.nw
+        for st in fac.stages:
+            ent = [(b.xidx.size * b.widx.size) if st.kind == omidbf.KIND_S else
+                   sum(s.T.size + s.skel.size for s in b.subs) for b in st.blocks]
+            pick = list(range(0, len(st.blocks), sample_every))
+            sub = omidbf.Stage(st.kind, st.in_space, st.out_len, st.out_user, [st.blocks[i] for i in pick])
+            M = omidbf.stage_matrix(fac, sub, in_len)
+            v = rng.standard_normal(in_len) + 1j * rng.standard_normal(in_len)
+            w = rng.standard_normal(st.out_len) + 1j * rng.standard_normal(st.out_len)
+            self.parts.append((M, M.conj().T.tocsr(), v, w))
+            total += sum(ent)
+            sampled += sum(ent[i] for i in pick)
+            in_len = st.out_len
+        self.scale = total / max(1, sampled)
+        self.desc = (f"every {sample_every}th block of each stage ({sampled} of {total} factor entries); "
+                     f"forward+adjoint sparse FP64 apply; time scaled by the entry ratio")
+
+    def step_seconds(self):
+        t0 = time.perf_counter()
+        for M, MH, v, w in self.parts:
+            M @ v
+            MH @ w
+        return (time.perf_counter() - t0) * self.scale
+
+
+def cpu_baseline(plan_bytes, n_points, seconds_budget=15.0):
+    smp = OracleSample(plan_bytes)
+    times = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds_budget or len(times) < 3:
+        times.append(smp.step_seconds())
+    step_s = statistics.median(times)
+    return {"value": 2 * n_points / step_s, "unit": "points*RHS/s", "cores": smp.cores, "kind": "oracle",
+            "sample": smp.desc + f"; median of {len(times)} repetitions"}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the CPU oracle's apply as it stands, on the host cores."""
+    if rank != 0:
+        return
+    import paper_1908_09376_gb300 as mb
+    X, W, bx, bw = workload(args.n)
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=64, boxX=bx, boxW=bw,
+                         nthreads=args.threads)
+    smp = OracleSample(plan.export())
+    del plan
+    N = args.n ** 2
+    for _ in range(args.warmup):
+        smp.step_seconds()
+    times = [smp.step_seconds() for _ in range(args.steps)]
+    step_s = sum(times) / len(times)
+    v = 2 * N / step_s
+    cpu = {"value": v, "unit": "points*RHS/s", "cores": smp.cores, "kind": "oracle", "sample": smp.desc}
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points*RHS/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": f"fio2d_n{args.n}", "N": N, "nrhs": 1, "tol": 1e-6, "n0": 64,
+                      "step": "forward + adjoint apply"},
+           "cpu_baseline": cpu, "e2e": {"value": v, "unit": "points*RHS/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import torch
+    import paper_1908_09376_gb300 as mb
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    n = args.n
+    N = n * n
+    X, W, bx, bw = workload(n)
+
+    t0 = time.perf_counter()
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    plan = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, nthreads=args.threads)
+    t_build = time.perf_counter() - t0
+    st = plan.stats()
+    t0 = time.perf_counter()
+    dp32 = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY)
+    t_up = time.perf_counter() - t0
+    fbytes, ibytes = dp32.bytes()
+
+    f = torch.from_numpy(synth.complex_gaussian(N, 1, 0)[:, 0]).to(dev, torch.complex64)
+    g = torch.empty(N, dtype=torch.complex64, device=dev)
+    h = torch.empty(N, dtype=torch.complex64, device=dev)
+    ws1 = torch.empty(dp32.workspace_bytes(1), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    launches_per_apply = dp32.launches()
+
+    def step():
+        dp32.apply(f, out=g, workspace=ws1)
+        dp32.apply(g, adjoint=True, out=h, workspace=ws1)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()                       # evict L2 between timed steps
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if pg:
+        tt = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        total_ms = tt.item()
+    ms_per_step = total_ms / args.steps
+    value = ws * 2 * N / (ms_per_step * 1e-3)
+
+    # the same steps again with CUDA events around every stage launch
+    dp32.profile(True)
+    stage_ms = {}
+    for i in range(args.steps):
+        flush.zero_()
+        dp32.apply(f, out=g, workspace=ws1)
+        for q, (kind, ms, by) in enumerate(dp32.stage_times()):
+            stage_ms.setdefault(("fwd", q, kind, by), []).append(ms)
+        dp32.apply(g, adjoint=True, out=h, workspace=ws1)
+        for q, (kind, ms, by) in enumerate(dp32.stage_times()):
+            stage_ms.setdefault(("adj", q, kind, by), []).append(ms)
+    dp32.profile(False)
+
+    # dominant kernel and its roofline (algorithmic bytes / event-timed duration)
+    peak, peak_kind = peaks()
+    dom = max(stage_ms.items(), key=lambda kv: statistics.mean(kv[1]))
+    (direction, q, kind, by), times = dom
+    dom_ms = statistics.mean(times)
+    achieved = by / (dom_ms * 1e-3) / 1e9
+    all_bytes = sum(k[3] for k in stage_ms.keys())
+    stage_rows = [{"dir": k[0], "stage": k[1], "kind": "VSU"[k[2]], "ms": round(statistics.mean(v), 4),
+                   "GB": round(k[3] / 1e9, 4), "GBps": round(k[3] / (statistics.mean(v) * 1e-3) / 1e9, 1)}
+                  for k, v in sorted(stage_ms.items(), key=lambda kv: (kv[0][0] != "fwd", kv[0][1]))]
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": f"{direction} stage {q} ({'VSU'[kind]})", "peak_source": peak_kind,
+                "whole_step_GBps": round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1),
+                "whole_step_frac": round(all_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+
+    extras = {}
+    if not args.skip_extras:
+        # plain FP64 form (middle factor stored: FP64 sincospi on GB300 is slow)
+        dp64 = mb.DevicePlan(plan, mb.FP64, mb.S_STORED)
+        f64 = f.to(torch.complex128)
+        g64 = torch.empty(N, dtype=torch.complex128, device=dev)
+        h64 = torch.empty(N, dtype=torch.complex128, device=dev)
+        ws64 = torch.empty(dp64.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            dp64.apply(f64, out=g64, workspace=ws64)
+            dp64.apply(g64, adjoint=True, out=h64, workspace=ws64)
+        torch.cuda.synchronize()
+        k64 = max(3, args.steps // 4)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot64 = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            e0.record(stream)
+            dp64.apply(f64, out=g64, workspace=ws64)
+            dp64.apply(g64, adjoint=True, out=h64, workspace=ws64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot64 += e0.elapsed_time(e1)
+        ms64 = tot64 / k64
+        dp32.apply(f, out=g, workspace=ws1)
+        dp32.apply(g, adjoint=True, out=h, workspace=ws1)
+        dp64.apply(g.to(torch.complex128), adjoint=True, out=h64, workspace=ws64)
+        torch.cuda.synchronize()
+        rel_fwd = (torch.linalg.vector_norm(g.to(torch.complex128) - g64) / torch.linalg.vector_norm(g64)).item()
+        rel_adj = (torch.linalg.vector_norm(h.to(torch.complex128) - h64) / torch.linalg.vector_norm(h64)).item()
+        extras["plain_fp64"] = {"value": 2 * N / (ms64 * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(ms64, 4),
+                                "s_mode": "stored", "bound": "alu(fp64)"}
+        extras["speedup_mixed_vs_plain"] = round(ms64 / ms_per_step, 3)
+        extras["rel_l2_fp32_vs_fp64"] = {"forward": rel_fwd, "adjoint": rel_adj}
+        del dp64, ws64
+        torch.cuda.empty_cache()
+        # 64 right-hand sides, FP32
+        R = 64
+        F = torch.from_numpy(synth.complex_gaussian(N, R, 0).T.copy()).to(dev, torch.complex64)
+        G = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        H = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        wsR = torch.empty(dp32.workspace_bytes(R), dtype=torch.uint8, device=dev)
+        dp32.apply(F, out=G, workspace=wsR)
+        torch.cuda.synchronize()
+        kR = 3
+        totR = 0.0
+        for _ in range(kR):
+            flush.zero_()
+            e0.record(stream)
+            dp32.apply(F, out=G, workspace=wsR)
+            dp32.apply(G, adjoint=True, out=H, workspace=wsR)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            totR += e0.elapsed_time(e1)
+        msR = totR / kR
+        extras["nrhs64_fp32"] = {"value": 2 * N * R / (msR * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msR, 3)}
+        del wsR, F, G, H
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    fh = torch.from_numpy(synth.complex_gaussian(N, 1, 0)[:, 0].astype(np.complex64)).pin_memory()
+    gh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    hh = torch.empty(N, dtype=torch.complex64).pin_memory()
+    wsh = torch.empty(dp32.workspace_bytes(1, host_io=True), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), 1, stream.cuda_stream,
+                                     wsh.data_ptr(), wsh.numel()), "apply_host")
+    ke = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(ke):
+        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), 1, stream.cuda_stream,
+                                     wsh.data_ptr(), wsh.numel()), "apply_host")
+        mb.check(mb.midbf_apply_host(dp32.h, 1, gh.data_ptr(), hh.data_ptr(), 1, stream.cuda_stream,
+                                     wsh.data_ptr(), wsh.numel()), "apply_host")
+    e2e_s = (time.perf_counter() - te) / ke
+    e2e = {"value": ws * 2 * N / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": 2 * N * 8,
+           "d2h_bytes_per_step": 2 * N * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_extras:
+        cpu = cpu_baseline(plan.export(), N)
+
+    out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": f"fio2d_n{n}", "N": N, "d": 2, "phase": "FIO2D closed form",
+                      "nrhs": 1, "step": "forward + adjoint apply", "tol": 1e-6, "n0": 64, "L": st["L"],
+                      "t_entries": st["t_entries"], "s_entries": st["s_entries"], "max_rank": st["max_rank"],
+                      "mean_rank": round(st["mean_rank"], 1), "factor_bytes": fbytes, "index_bytes": ibytes,
+                      "l2": "flushed (512 MB write) between timed steps; factors 3+ GB > L2",
+                      "parallelism": f"replicas x{ws}", "build_s": round(t_build, 1),
+                      "upload_s": round(t_up, 1)},
+           "roofline": roofline, "stages": stage_rows, "clocks": clk, "e2e": e2e,
+           "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
+    out.update(extras)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

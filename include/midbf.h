@@ -1,0 +1,235 @@
+/*
+ * midbf.h - C ABI of the GB300 MIDBF library.
+ *
+ * The library applies the multidimensional interpolative decomposition
+ * butterfly factorization (MIDBF) of K(x, xi) = exp(2 pi i Phi(x, xi)) and of
+ * its adjoint to vectors on one GPU (Chen, Zhang, Ho, Yang, "Multidimensional
+ * Phase Recovery and Interpolative Decomposition Butterfly Factorization").
+ * The calls follow the paper's statement of the problem (Sec. 1, eq. (1)):
+ *
+ *   1. a phase Phi: a closed form (Scenario 1 of Table 1), a low-rank factor
+ *      pair Psi = U V^T, or one recovered from a few rows and columns of K
+ *      (Scenario 2, Algorithm 7);
+ *   2. midbf_build: the butterfly factors from kernel samples (Sec. 3);
+ *   3. midbf_dplan_create + midbf_apply: g = K f or f = K^H g on the GPU.
+ *
+ * Conventions for every function:
+ *   - Return value: MIDBF_OK (0) or a negative MIDBF_E* code.  On failure a
+ *     human-readable message is available from midbf_last_error() (per
+ *     thread) and no output handle is written.
+ *   - Handles (midbf_phase, midbf_plan, midbf_dplan) are owned by the caller
+ *     after creation and released with the matching *_destroy call.  Host
+ *     arrays passed in are copied; the library keeps no pointer to them.
+ *   - Indices are 0-based.  Coordinates are row-major (n x d) doubles.
+ *   - Complex vectors are interleaved (re, im) pairs: double (complex128) for
+ *     MIDBF_FP64, float (complex64) for MIDBF_FP32.  Multiple right-hand sides
+ *     are stored column-major: entry p of RHS r at offset r * ld + p.
+ *   - Nothing here falls back to the CPU: apply calls need a CUDA device and
+ *     fail with MIDBF_ECUDA when none is present.
+ */
+#ifndef MIDBF_H
+#define MIDBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MIDBF_OK          0
+#define MIDBF_EINVAL     -1   /* bad argument, size or handle                 */
+#define MIDBF_ENOMEM     -2   /* host or device allocation failed             */
+#define MIDBF_ECUDA      -3   /* a CUDA runtime call failed / no device        */
+#define MIDBF_ECALLBACK  -4   /* a caller-supplied access callback failed      */
+#define MIDBF_ERANK      -5   /* a rank cap was hit before the tolerance       */
+#define MIDBF_ERECOVERY  -6   /* phase recovery could not proceed              */
+#define MIDBF_ETIMEOUT   -7   /* a device-side bounded wait gave up            */
+#define MIDBF_EINTERNAL  -8   /* inconsistent plan or internal error           */
+#define MIDBF_EFORMAT    -9   /* malformed plan file                           */
+
+/* ---- phase families (Scenario 1 closed forms) -------------------------- */
+#define MIDBF_PHASE_FIO2D       1 /* x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), Sec. 4 Example 1 */
+#define MIDBF_PHASE_FIO3D       2 /* x.xi + sqrt(sum c_k^2 xi_k^2), c_k=(2+sin2pi x_k cos2pi x_{k+1})/16 */
+#define MIDBF_PHASE_FIO2D_JUMP  3 /* FIO2D + 0.5 |xi| sign(x1 - 0.5), sign(0) = +1 */
+#define MIDBF_PHASE_DOT         4 /* x.xi (Fourier, Sec. 4 Example 2)              */
+#define MIDBF_PHASE_ZERO        5 /* 0 (rank-one K)                                */
+#define MIDBF_PHASE_SEPARABLE   6 /* sum_k sin(2 pi x_k) + 0.05 sum_k xi_k^2        */
+#define MIDBF_PHASE_LOWRANK     7 /* Psi(i, j) = sum_t U[i,t] V[j,t] (Algorithm 7)  */
+
+/* ---- apply precisions -------------------------------------------------- */
+#define MIDBF_FP64  0   /* plain form: complex128 data and arithmetic          */
+#define MIDBF_FP32  1   /* mixed form: complex64 data and arithmetic           */
+
+/* ---- middle-factor modes ----------------------------------------------- */
+#define MIDBF_S_ONTHEFLY 0  /* S entries exp(2 pi i Phi) generated in the kernel */
+#define MIDBF_S_STORED   1  /* S entries precomputed once at dplan creation      */
+
+typedef struct midbf_phase midbf_phase;  /* phase function over (X, Omega)   */
+typedef struct midbf_plan midbf_plan;    /* host butterfly factors (immutable) */
+typedef struct midbf_dplan midbf_dplan;  /* device-resident copy of a plan    */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* midbf_last_error(void);
+
+/* Library version string. */
+const char* midbf_version(void);
+
+/* ---- phases -------------------------------------------------------------
+ * midbf_phase_closed_form: Phi of one of the MIDBF_PHASE_* closed forms over
+ * the point sets X (nx x d) and W (nw x d), d = 2 or 3.  FIO2D/FIO2D_JUMP need
+ * d = 2, FIO3D needs d = 3.  Errors: MIDBF_EINVAL.
+ */
+int midbf_phase_closed_form(int family, int d, int64_t nx, const double* X,
+                            int64_t nw, const double* W, midbf_phase** out);
+
+/* midbf_phase_lowrank: Psi(i, j) = sum_t U[i*r + t] V[j*r + t] (U nx x r,
+ * V nw x r, row-major), the output form of Algorithm 7 (Sec. 2.3).  X and W
+ * are still required: the butterfly trees are built over them. */
+int midbf_phase_lowrank(int d, int64_t nx, const double* X, int64_t nw, const double* W,
+                        int r, const double* U, const double* V, midbf_phase** out);
+
+/* Indirect access to K (Scenario 2 of Table 1): rows_fn writes K(idx[c], :)
+ * for c < cnt into out[c * nw + j] (interleaved complex128); cols_fn writes
+ * K(:, idx[c]) into out[c * nx + i].  Return 0 on success, nonzero to abort
+ * (reported as MIDBF_ECALLBACK). */
+typedef int (*midbf_rows_fn)(void* user, const int64_t* idx, int64_t cnt, double* out);
+typedef struct {
+    midbf_rows_fn rows_fn;
+    midbf_rows_fn cols_fn;
+    void* user;
+} midbf_access;
+
+typedef struct {
+    int64_t rows_requested;   /* rows fetched through rows_fn                  */
+    int64_t cols_requested;   /* columns fetched through cols_fn               */
+    int64_t disc_rows;        /* |D_r| - 1: discontinuities found along X      */
+    int64_t disc_cols;        /* |D_c| - 1                                      */
+    double tau;               /* detection threshold finally used              */
+    int64_t mismatches;       /* recovered rows and columns disagreeing (Lemma 3.2) */
+} midbf_recover_info;
+
+/* midbf_phase_recover: Algorithm 7 (with Algorithms 1, 4, 5, 6).  Samples
+ * r*q rows and columns (index 0 plus seeded random ones), recovers them along
+ * Euclidean-MST recovery paths of X and W (Def. 3.3), and factors the result
+ * with the restricted randomized SVD into a rank-r phase.  tau: initial
+ * discontinuity threshold (paper: 1/4), raised by 1/40 while more than
+ * max_disc discontinuities are found, at most to 1/2.  info may be NULL.
+ * Errors: MIDBF_EINVAL, MIDBF_ECALLBACK, MIDBF_ERECOVERY. */
+int midbf_phase_recover(int d, int64_t nx, const double* X, int64_t nw, const double* W,
+                        const midbf_access* acc, int r, int q, double tau, int max_disc,
+                        uint64_t seed, midbf_phase** out, midbf_recover_info* info);
+
+/* Evaluate Phi at n index pairs (ix[c], iw[c]) into out[c] (host, FP64). */
+int midbf_phase_eval(const midbf_phase* ph, int64_t n, const int64_t* ix, const int64_t* iw,
+                     double* out);
+
+/* Rank r of a low-rank phase (0 for closed forms); copies U, V when not NULL. */
+int midbf_phase_factors(const midbf_phase* ph, int* r, double* U, double* V);
+
+void midbf_phase_destroy(midbf_phase* ph);
+
+/* ---- construction (Sec. 3) ------------------------------------------------
+ * Parameters of midbf_build.  midbf_params_default fills the paper's choices
+ * (Sec. 4: eps = 1e-9, n0 = 8^d, t = 5) adjusted as documented: t = 2 with the
+ * sample regrown to t * k_eps rows, kest = 30 (2D) / 80 (3D). */
+typedef struct {
+    double tol;        /* relative ID tolerance eps (Sec. 3.6)                  */
+    int n0;            /* target points per leaf; depth L = round(log_b(N/n0))  */
+    double t;          /* oversampling: sample >= t * k_eps rows (Sec. 3.2)     */
+    int kest;          /* initial rank estimate k                               */
+    int kmax;          /* rank cap, 0 = none (cap reached -> still succeeds)    */
+    uint64_t seed;     /* seed of the random top-up of Mock-Chebyshev samples   */
+    int nthreads;      /* host threads, 0 = all cores                           */
+    int use_box;       /* 1: use boxX/boxW as the tree domains, 0: tight cubes  */
+    double boxX[4];    /* lo[0..d-1], side (at index d)                         */
+    double boxW[4];
+} midbf_params;
+
+int midbf_params_default(int d, midbf_params* p);
+
+/* Build the butterfly factors of K = exp(2 pi i Phi) over the phase's point
+ * sets.  Host FP64 (pivoted QRs and kernel samples).  Errors: MIDBF_EINVAL,
+ * MIDBF_ENOMEM. */
+int midbf_build(const midbf_phase* ph, const midbf_params* p, midbf_plan** out);
+
+/* Serialize a plan into the level-program file format; *buf is allocated with
+ * malloc and released by the caller with midbf_free. */
+int midbf_plan_export(const midbf_plan* plan, void** buf, size_t* len);
+
+/* Read a plan file (from this library or any writer of the same format).
+ * The plan is validated (every index in range, every output written once).
+ * Errors: MIDBF_EFORMAT, MIDBF_ENOMEM. */
+int midbf_plan_import(const void* buf, size_t len, midbf_plan** out);
+
+typedef struct {
+    int d, L, delta, nsteps, nstages;
+    int64_t nx, nw;
+    int64_t nblocks;         /* blocks over all stages                         */
+    int64_t nsubs;           /* interpolative decompositions                   */
+    int64_t t_entries;       /* stored interpolation entries (T parts)         */
+    int64_t skel_entries;    /* identity (skeleton) entries, not stored        */
+    int64_t s_entries;       /* middle-factor entries (generated or stored)    */
+    int64_t index_entries;   /* gather/scatter position entries                */
+    int max_rank;
+    double mean_rank;
+} midbf_stats;
+
+int midbf_plan_stats(const midbf_plan* plan, midbf_stats* st);
+void midbf_plan_destroy(midbf_plan* plan);
+void midbf_free(void* p);
+
+/* ---- device plans and the apply ----------------------------------------
+ * midbf_dplan_create: copy a plan to the current CUDA device in one precision
+ * (MIDBF_FP64 or MIDBF_FP32) and middle-factor mode.  Allocates device memory
+ * (cudaMalloc) and synchronizes the device; call before any stream capture.
+ * Errors: MIDBF_EINVAL, MIDBF_ENOMEM, MIDBF_ECUDA. */
+int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out);
+void midbf_dplan_destroy(midbf_dplan* dp);
+
+/* Bytes of device workspace midbf_apply needs for nrhs right-hand sides. */
+int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes);
+
+/* Device bytes held by the plan's factors and index maps (for roofline use):
+ * bytes the apply must stream once per call, per direction. */
+int midbf_dplan_bytes(const midbf_dplan* dp, size_t* factor_bytes, size_t* index_bytes);
+
+/* midbf_apply: out = K in (adjoint = 0; in has nw entries, out nx) or
+ * out = K^H in (adjoint = 1; in nx, out nw), for nrhs right-hand sides, on
+ * the CUDA stream `stream` (cudaStream_t, NULL = legacy default stream).
+ * in/out are device pointers with leading dimensions ldin/ldout (>= vector
+ * length); they must not overlap.  workspace: device memory of at least
+ * midbf_workspace_size bytes, owned by the caller, not shared between calls
+ * in flight.  Asynchronous: argument errors are returned immediately; device
+ * faults surface through later CUDA calls.  Allocates nothing.
+ * Errors: MIDBF_EINVAL, MIDBF_ECUDA. */
+int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin,
+                void* out, int64_t ldout, int nrhs, void* stream,
+                void* workspace, size_t workspace_bytes);
+
+/* midbf_apply_host: as midbf_apply with HOST in/out buffers (ideally pinned):
+ * copies in to the device, applies, copies out back, all on `stream`, then
+ * synchronizes the stream.  The workspace must hold
+ * midbf_workspace_size + (nx + nw) * nrhs complex entries. */
+int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, void* out_host,
+                     int nrhs, void* stream, void* workspace, size_t workspace_bytes);
+
+/* Number of kernel launches one midbf_apply issues (for launch accounting). */
+int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches);
+
+/* Per-stage timing for measurement: with enable = 1, every later midbf_apply
+ * on this dplan records a CUDA event on its stream before and after each
+ * stage launch (calls must then not overlap).  midbf_stage_times waits for
+ * the events of the most recent apply and writes up to max_stages durations
+ * in milliseconds, in launch order, with the stage kind (0 = V, 1 = S, 2 = U)
+ * and the number of algorithmic bytes the stage streams (factor entries,
+ * index maps, input and output vectors) per right-hand side batch. */
+int midbf_dplan_profile(midbf_dplan* dp, int enable);
+int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kinds, double* bytes,
+                      int* n_stages);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MIDBF_H */

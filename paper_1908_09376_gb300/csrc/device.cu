@@ -1,0 +1,685 @@
+// Device-resident plans and the apply launcher (host code + kernel launches).
+//
+// midbf_dplan_create turns a host plan (factor stages of eq. (finishIDBF),
+// Sec. 3.5) into device arrays in one precision:
+//   * ID blocks: T of every interpolative decomposition (Sec. 3.2) column-major
+//     with its redundant indices sorted ascending, block/sub descriptors, the
+//     wide/narrow position maps and the work-item lists of both patterns;
+//   * the middle factor: per-entry phase-split data for on-the-fly generation
+//     (or the dense entries, MIDBF_S_STORED).
+// midbf_apply runs the stages in order (forward) or reverse order with
+// conjugated factors (adjoint), ping-ponging between two workspace vectors.
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+#include <numeric>
+#include <thread>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+
+using namespace midbf;
+using namespace midbf_dev;
+
+namespace {
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) fail(MIDBF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kRangeC = 64;   // output entries per pattern-C item
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct DevStageBase {
+    int kind = KIND_V;
+    int64_t in_len = 0, out_len = 0;
+    bool out_user = false, in_user = false;
+};
+
+template <class R>
+struct DevStage : DevStageBase {
+    // ID stages (and stored S)
+    bool id = false;
+    IdStage<R> ids{};
+    int n_items_r = 0, n_items_c = 0, rt = 1;
+    size_t smem_r = 0, smem_c = 0;
+    // on-the-fly S
+    SStage<R> ss{};
+    SSide<R> srows{}, scols{};
+    const int2* items_rows = nullptr;
+    const int2* items_cols = nullptr;
+    int n_items_rows = 0, n_items_cols = 0, rt_rows = 1, rt_cols = 1;
+    size_t smem_rows = 0, smem_cols = 0;
+};
+
+}  // namespace
+
+struct midbf_dplan {
+    int precision = MIDBF_FP32;
+    int s_mode = MIDBF_S_ONTHEFLY;
+    int device = 0;
+    int64_t nx = 0, nw = 0;
+    int64_t max_space = 0;        // longest internal vector space
+    size_t factor_bytes = 0, index_bytes = 0;
+    std::vector<void*> allocs;
+    std::vector<DevStage<float>> st32;
+    std::vector<DevStage<double>> st64;
+    int launches = 0;
+    // per stage, in forward order: stored bytes streamed once per apply, and
+    // the input + output vector lengths (entries per right-hand side)
+    std::vector<double> stage_fixed_bytes;
+    std::vector<int64_t> stage_vec_entries;
+    std::vector<int> stage_kind;
+    // measurement hooks (midbf_dplan_profile / midbf_stage_times)
+    bool profile = false;
+    mutable std::vector<cudaEvent_t> ev;
+    mutable std::vector<int> ev_stage;   // stage index of each event pair of the last apply
+    mutable int last_nrhs = 1;
+    ~midbf_dplan() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace {
+
+template <class T>
+T* upload(midbf_dplan* dp, const std::vector<T>& v, size_t* counter) {
+    if (v.empty()) return nullptr;
+    void* p = nullptr;
+    size_t bytes = v.size() * sizeof(T);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) fail(MIDBF_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    dp->allocs.push_back(p);
+    CK(cudaMemcpy(p, v.data(), bytes, cudaMemcpyHostToDevice));
+    if (counter) *counter += bytes;
+    return static_cast<T*>(p);
+}
+
+inline double frac(double v) { return v - std::nearbyint(v); }
+
+int rows_per_lane(int maxk) { return maxk <= 32 ? 1 : 2; }
+
+// Build the device arrays of an ID stage (V or U), or of a stored S stage
+// seen as dense blocks with no skeleton.
+template <class R>
+void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds, bool stored_s) {
+    std::vector<SubDesc> subs;
+    std::vector<BlockDesc> blocks;
+    std::vector<int> skel, red, wide_pos, narrow_pos;
+    std::vector<ItemR> items_r;
+    std::vector<ItemC> items_c;
+    std::vector<cx<R>> T;
+    int maxk = 1;
+    size_t max_nred = 0, max_narrow = 0, max_nsub = 1;
+    const bool is_v = st.kind == KIND_V || st.kind == KIND_S;  // S stored: wide = input like V
+    for (size_t b = 0; b < st.blocks.size(); ++b) {
+        const Block& bk = st.blocks[b];
+        BlockDesc bd{};
+        const std::vector<int64_t>& wide = is_v ? bk.in_idx : bk.out_idx;
+        const std::vector<int64_t>& narrow = is_v ? bk.out_idx : bk.in_idx;
+        bd.m = (int)wide.size();
+        bd.wide_off = (int)wide_pos.size();
+        bd.narrow_off = (int)narrow_pos.size();
+        bd.nnarrow = (int)narrow.size();
+        bd.sub0 = (int)subs.size();
+        for (int64_t v : wide) wide_pos.push_back((int)v);
+        for (int64_t v : narrow) narrow_pos.push_back((int)v);
+        int noff = bd.narrow_off;
+        if (stored_s) {
+            // dense block: one "sub" with k = nrow rows, all columns redundant
+            SubDesc sd{};
+            sd.k = (int)bk.out_idx.size();
+            sd.nskel = 0;
+            sd.skel_off = (int)skel.size();
+            sd.red_off = (int)red.size();
+            sd.narrow_off = noff;
+            sd.block = (int)b;
+            sd.t_off = (long long)T.size();
+            for (int j = 0; j < bd.m; ++j) red.push_back(j);
+            const size_t base = T.size();
+            T.resize(base + (size_t)sd.k * bd.m);
+            const int nthreads = std::max(1u, std::thread::hardware_concurrency());
+            std::vector<std::thread> th;
+            for (int w = 0; w < nthreads; ++w)
+                th.emplace_back([&, w]() {
+                    for (int j = w; j < bd.m; j += nthreads)
+                        for (int i = 0; i < sd.k; ++i) {
+                            cplx kv = pl.phase.kernel(bk.xidx[i], bk.widx[j]);
+                            T[base + (size_t)j * sd.k + i] = {(R)kv.real(), (R)kv.imag()};
+                        }
+                });
+            for (auto& t : th) t.join();
+            subs.push_back(sd);
+            maxk = std::max(maxk, sd.k);
+            max_nred = std::max(max_nred, (size_t)bd.m);
+        } else {
+            for (const Sub& sb : bk.subs) {
+                SubDesc sd{};
+                sd.k = sb.k;
+                sd.nskel = sb.k;
+                sd.skel_off = (int)skel.size();
+                sd.red_off = (int)red.size();
+                sd.narrow_off = noff;
+                sd.block = (int)b;
+                sd.t_off = (long long)T.size();
+                noff += sb.k;
+                for (int v : sb.skel) skel.push_back(v);
+                const int nred = sb.m - sb.k;
+                std::vector<int> perm(nred);
+                std::iota(perm.begin(), perm.end(), 0);
+                std::sort(perm.begin(), perm.end(), [&](int a, int c) { return sb.red[a] < sb.red[c]; });
+                for (int jj = 0; jj < nred; ++jj) red.push_back(sb.red[perm[jj]]);
+                for (int jj = 0; jj < nred; ++jj)
+                    for (int i = 0; i < sb.k; ++i) {
+                        const cplx& v = sb.T[(size_t)i * nred + perm[jj]];
+                        T.push_back({(R)v.real(), (R)v.imag()});
+                    }
+                subs.push_back(sd);
+                maxk = std::max(maxk, sb.k);
+                max_nred = std::max(max_nred, (size_t)nred);
+            }
+        }
+        bd.nsub = (int)subs.size() - bd.sub0;
+        max_nsub = std::max(max_nsub, (size_t)bd.nsub);
+        max_narrow = std::max(max_narrow, (size_t)bd.nnarrow);
+        blocks.push_back(bd);
+        for (int o0 = 0; o0 < bd.m; o0 += kRangeC) items_c.push_back({(int)b, o0, std::min(bd.m, o0 + kRangeC), 0});
+    }
+    if (max_nsub > 16) fail(MIDBF_EINTERNAL, "more than 16 sub-blocks in a block");
+    const int rt = rows_per_lane(maxk);
+    for (size_t s = 0; s < subs.size(); ++s)
+        for (int r0 = 0; r0 < subs[s].k; r0 += 32 * rt) items_r.push_back({(int)s, r0});
+    ds.id = true;
+    ds.rt = rt;
+    ds.n_items_r = (int)items_r.size();
+    ds.n_items_c = (int)items_c.size();
+    ds.smem_r = (max_nred + (size_t)kWarps * 32 * rt) * sizeof(cx<R>);
+    ds.smem_c = (max_narrow + max_nsub * kRangeC) * sizeof(cx<R>);
+    if (ds.smem_r > 200 * 1024 || ds.smem_c > 200 * 1024) fail(MIDBF_EINTERNAL, "block too wide for shared memory");
+    ds.ids.subs = upload(dp, subs, &dp->index_bytes);
+    ds.ids.blocks = upload(dp, blocks, &dp->index_bytes);
+    ds.ids.skel = upload(dp, skel, &dp->index_bytes);
+    ds.ids.red = upload(dp, red, &dp->index_bytes);
+    ds.ids.wide_pos = upload(dp, wide_pos, &dp->index_bytes);
+    ds.ids.narrow_pos = upload(dp, narrow_pos, &dp->index_bytes);
+    ds.ids.T = upload(dp, T, &dp->factor_bytes);
+    ds.ids.items_r = upload(dp, items_r, &dp->index_bytes);
+    ds.ids.items_c = upload(dp, items_c, &dp->index_bytes);
+}
+
+// Split of the phase for one S block (see kernels.cuh): rows get (a, u, C),
+// columns (b, v, W), all computed in FP64 and rounded to R at the end.
+struct SplitOut {
+    std::vector<double> a, u, c;
+};
+
+void phase_split(const Phase& ph, const Block& bk, int P, int Q, SplitOut& rows, SplitOut& cols) {
+    const int d = ph.d;
+    const int64_t i0 = bk.xidx[0], j0 = bk.widx[0];
+    const size_t nr = bk.xidx.size(), nc = bk.widx.size();
+    rows.a.resize(nr);
+    rows.u.resize(nr * P);
+    rows.c.resize(nr * Q);
+    cols.a.resize(nc);
+    cols.u.resize(nc * P);
+    cols.c.resize(nc * Q);
+    const int fam = ph.family;
+    if (fam == MIDBF_PHASE_LOWRANK) {
+        const double* U0 = &ph.U[(size_t)i0 * ph.r];
+        const double* V0 = &ph.V[(size_t)j0 * ph.r];
+        for (size_t i = 0; i < nr; ++i) {
+            const double* Ui = &ph.U[(size_t)bk.xidx[i] * ph.r];
+            double s = 0.0;
+            for (int t = 0; t < ph.r; ++t) {
+                s += (Ui[t] - U0[t]) * V0[t];
+                rows.u[i * P + t] = Ui[t] - U0[t];
+            }
+            rows.a[i] = frac(s);
+        }
+        for (size_t j = 0; j < nc; ++j) {
+            const double* Vj = &ph.V[(size_t)bk.widx[j] * ph.r];
+            double s = 0.0;
+            for (int t = 0; t < ph.r; ++t) {
+                s += U0[t] * Vj[t];
+                cols.u[j * P + t] = Vj[t] - V0[t];
+            }
+            cols.a[j] = frac(s);
+        }
+        return;
+    }
+    if (fam == MIDBF_PHASE_ZERO || fam == MIDBF_PHASE_SEPARABLE) {
+        // Phi = a(x) + b(xi): a split with no mixed term
+        const double z[3] = {0, 0, 0};
+        for (size_t i = 0; i < nr; ++i) {
+            double v = ph.eval_xy(&ph.X[(size_t)bk.xidx[i] * d], z);
+            rows.a[i] = frac(v);
+        }
+        for (size_t j = 0; j < nc; ++j) {
+            double v = ph.eval_xy(z, &ph.W[(size_t)bk.widx[j] * d]) - ph.eval_xy(z, z);
+            cols.a[j] = frac(v);
+        }
+        return;
+    }
+    // DOT and FIO families: x.xi = x0.xi + (x - x0).xi0 + (x - x0).(xi - xi0)
+    const double* x0 = &ph.X[(size_t)i0 * d];
+    const double* w0 = &ph.W[(size_t)j0 * d];
+    const bool jump = fam == MIDBF_PHASE_FIO2D_JUMP;
+    const double sg0 = (x0[0] - 0.5 >= 0.0) ? 1.0 : -1.0;
+    const double twopi = 2.0 * M_PI;
+    for (size_t i = 0; i < nr; ++i) {
+        const double* x = &ph.X[(size_t)bk.xidx[i] * d];
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) {
+            s += (x[k] - x0[k]) * w0[k];
+            rows.u[i * P + k] = x[k] - x0[k];
+        }
+        rows.a[i] = frac(s);
+        if (jump) rows.u[i * P + d] = 0.5 * (((x[0] - 0.5 >= 0.0) ? 1.0 : -1.0) - sg0);
+        if (Q) {
+            if (d == 2) {
+                const double c1 = (2.0 + std::sin(twopi * x[0]) * std::sin(twopi * x[1])) / 16.0;
+                const double c2 = (2.0 + std::cos(twopi * x[0]) * std::cos(twopi * x[1])) / 16.0;
+                rows.c[i * Q + 0] = c1 * c1;
+                rows.c[i * Q + 1] = c2 * c2;
+            } else {
+                for (int k = 0; k < 3; ++k) {
+                    const double ck = (2.0 + std::sin(twopi * x[k]) * std::cos(twopi * x[(k + 1) % 3])) / 16.0;
+                    rows.c[i * Q + k] = ck * ck;
+                }
+            }
+        }
+    }
+    for (size_t j = 0; j < nc; ++j) {
+        const double* w = &ph.W[(size_t)bk.widx[j] * d];
+        double s = 0.0, nrm = 0.0;
+        for (int k = 0; k < d; ++k) {
+            s += x0[k] * w[k];
+            cols.u[j * P + k] = w[k] - w0[k];
+            nrm += w[k] * w[k];
+            if (Q) cols.c[j * Q + k] = w[k] * w[k];
+        }
+        if (jump) {
+            nrm = std::sqrt(nrm);
+            s += 0.5 * nrm * sg0;
+            cols.u[j * P + d] = frac(nrm) < 0 ? frac(nrm) + 1.0 : frac(nrm);
+        }
+        cols.a[j] = frac(s);
+    }
+}
+
+template <class R>
+void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds) {
+    const Phase& ph = pl.phase;
+    int P = 0, Q = 0;
+    switch (ph.family) {
+        case MIDBF_PHASE_LOWRANK: P = ph.r; break;
+        case MIDBF_PHASE_DOT: P = ph.d; break;
+        case MIDBF_PHASE_FIO2D: case MIDBF_PHASE_FIO3D: P = ph.d; Q = ph.d; break;
+        case MIDBF_PHASE_FIO2D_JUMP: P = ph.d + 1; Q = ph.d; break;
+        default: break;
+    }
+    if (P > 8 || Q > 3) fail(MIDBF_EINVAL, "on-the-fly middle factor supports at most 8 low-rank terms");
+    std::vector<int> blk_rows, blk_cols, blk_nrow, blk_ncol, rpos, cpos;
+    std::vector<R> ra, ru, rc, ca, cu, cc;
+    std::vector<int2> it_rows, it_cols;
+    int maxr = 1, maxc = 1;
+    for (size_t b = 0; b < st.blocks.size(); ++b) {
+        const Block& bk = st.blocks[b];
+        SplitOut r, c;
+        phase_split(ph, bk, P, Q, r, c);
+        blk_rows.push_back((int)ra.size());
+        blk_cols.push_back((int)ca.size());
+        blk_nrow.push_back((int)bk.xidx.size());
+        blk_ncol.push_back((int)bk.widx.size());
+        maxr = std::max(maxr, (int)bk.xidx.size());
+        maxc = std::max(maxc, (int)bk.widx.size());
+        for (double v : r.a) ra.push_back((R)v);
+        for (double v : r.u) ru.push_back((R)v);
+        for (double v : r.c) rc.push_back((R)v);
+        for (double v : c.a) ca.push_back((R)v);
+        for (double v : c.u) cu.push_back((R)v);
+        for (double v : c.c) cc.push_back((R)v);
+        for (int64_t v : bk.out_idx) rpos.push_back((int)v);
+        for (int64_t v : bk.in_idx) cpos.push_back((int)v);
+    }
+    ds.rt_rows = rows_per_lane(maxr);
+    ds.rt_cols = rows_per_lane(maxc);
+    for (size_t b = 0; b < st.blocks.size(); ++b) {
+        for (int r0 = 0; r0 < blk_nrow[b]; r0 += 32 * ds.rt_rows) it_rows.push_back(make_int2((int)b, r0));
+        for (int c0 = 0; c0 < blk_ncol[b]; c0 += 32 * ds.rt_cols) it_cols.push_back(make_int2((int)b, c0));
+    }
+    ds.ss.P = P;
+    ds.ss.Q = Q;
+    ds.ss.blk_rows = upload(dp, blk_rows, &dp->index_bytes);
+    ds.ss.blk_cols = upload(dp, blk_cols, &dp->index_bytes);
+    ds.ss.blk_nrow = upload(dp, blk_nrow, &dp->index_bytes);
+    ds.ss.blk_ncol = upload(dp, blk_ncol, &dp->index_bytes);
+    ds.srows.a = upload(dp, ra, &dp->factor_bytes);
+    ds.srows.u = upload(dp, ru, &dp->factor_bytes);
+    ds.srows.c = upload(dp, rc, &dp->factor_bytes);
+    ds.srows.pos = upload(dp, rpos, &dp->index_bytes);
+    ds.scols.a = upload(dp, ca, &dp->factor_bytes);
+    ds.scols.u = upload(dp, cu, &dp->factor_bytes);
+    ds.scols.c = upload(dp, cc, &dp->factor_bytes);
+    ds.scols.pos = upload(dp, cpos, &dp->index_bytes);
+    ds.items_rows = upload(dp, it_rows, &dp->index_bytes);
+    ds.items_cols = upload(dp, it_cols, &dp->index_bytes);
+    ds.n_items_rows = (int)it_rows.size();
+    ds.n_items_cols = (int)it_cols.size();
+    ds.smem_rows = s_fly_smem<R>(P, Q, ds.rt_rows);
+    ds.smem_cols = s_fly_smem<R>(P, Q, ds.rt_cols);
+}
+
+template <class R>
+void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out) {
+    int64_t in_len = pl.phase.nw;
+    for (size_t s = 0; s < pl.stages.size(); ++s) {
+        const Stage& st = pl.stages[s];
+        DevStage<R> ds;
+        ds.kind = st.kind;
+        ds.in_len = in_len;
+        ds.out_len = st.out_len;
+        ds.in_user = s == 0;
+        ds.out_user = st.out_user != 0;
+        const size_t f0 = dp->factor_bytes, i0 = dp->index_bytes;
+        if (st.kind == KIND_S) {
+            if (dp->s_mode == MIDBF_S_STORED) make_id_stage<R>(dp, pl, st, ds, true);
+            else make_s_stage<R>(dp, pl, st, ds);
+        } else {
+            make_id_stage<R>(dp, pl, st, ds, false);
+        }
+        // algorithmic bytes: factor data and position maps once, vectors per RHS
+        // (work-item lists and descriptors are bookkeeping, counted too)
+        dp->stage_fixed_bytes.push_back((double)(dp->factor_bytes - f0) + (double)(dp->index_bytes - i0));
+        dp->stage_vec_entries.push_back(in_len + st.out_len);
+        dp->stage_kind.push_back(st.kind);
+        if (!ds.in_user) dp->max_space = std::max(dp->max_space, in_len);
+        if (!ds.out_user) dp->max_space = std::max(dp->max_space, st.out_len);
+        in_len = st.out_len;
+        out.push_back(std::move(ds));
+    }
+}
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <class R>
+void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
+    if (ds.n_items_r == 0) return;
+#define LR(RT, CJ)                                                                                   \
+    {                                                                                                \
+        auto kf = k_pattern_r<R, RT, CJ>;                                                            \
+        set_smem(kf, ds.smem_r);                                                                     \
+        kf<<<ds.n_items_r, kThreads, ds.smem_r, s>>>(ds.ids, src, dst, nrhs);                        \
+    }
+    if (ds.rt == 1) {
+        if (conj) LR(1, true) else LR(1, false)
+    } else {
+        if (conj) LR(2, true) else LR(2, false)
+    }
+#undef LR
+    CK(cudaGetLastError());
+}
+
+template <class R>
+void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
+    if (ds.n_items_c == 0) return;
+    if (conj) {
+        auto kf = k_pattern_c<R, true>;
+        set_smem(kf, ds.smem_c);
+        kf<<<ds.n_items_c, kThreads, ds.smem_c, s>>>(ds.ids, src, dst, nrhs, kRangeC);
+    } else {
+        auto kf = k_pattern_c<R, false>;
+        set_smem(kf, ds.smem_c);
+        kf<<<ds.n_items_c, kThreads, ds.smem_c, s>>>(ds.ids, src, dst, nrhs, kRangeC);
+    }
+    CK(cudaGetLastError());
+}
+
+template <class R>
+void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s) {
+    SStage<R> st = ds.ss;
+    if (!adjoint) {
+        st.items = ds.items_rows;
+#define LS(RT)                                                                                         \
+    {                                                                                                  \
+        auto kf = k_s_fly<R, RT, false>;                                                               \
+        set_smem(kf, ds.smem_rows);                                                                    \
+        kf<<<ds.n_items_rows, kThreads, ds.smem_rows, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs); \
+    }
+        if (ds.rt_rows == 1) LS(1) else LS(2)
+#undef LS
+    } else {
+        st.items = ds.items_cols;
+#define LS(RT)                                                                                         \
+    {                                                                                                  \
+        auto kf = k_s_fly<R, RT, true>;                                                                \
+        set_smem(kf, ds.smem_cols);                                                                    \
+        kf<<<ds.n_items_cols, kThreads, ds.smem_cols, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs); \
+    }
+        if (ds.rt_cols == 1) LS(1) else LS(2)
+#undef LS
+    }
+    CK(cudaGetLastError());
+}
+
+template <class R>
+int count_launches(const std::vector<DevStage<R>>& st) {
+    int n = 0;
+    for (auto& s : st) n += 1;
+    return n;
+}
+
+// Run all stages.  user_in/user_out: caller vectors (column-major with ld).
+template <class R>
+void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adjoint, const void* in, int64_t ldin,
+         void* out, int64_t ldout, int nrhs, cudaStream_t s, void* ws) {
+    const int ns = (int)stages.size();
+    cx<R>* buf[2] = {static_cast<cx<R>*>(ws), static_cast<cx<R>*>(ws) + dp->max_space * nrhs};
+    VecRef<R> uin{(cx<R>*)in, 1, ldin};
+    VecRef<R> uout{(cx<R>*)out, 1, ldout};
+    auto internal = [&](int space) { return VecRef<R>{buf[space & 1], nrhs, 1}; };
+    if (dp->profile) {
+        while ((int)dp->ev.size() < 2 * ns) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            dp->ev.push_back(e);
+        }
+        dp->ev_stage.assign(ns, 0);
+        dp->last_nrhs = nrhs;
+    }
+    for (int q = 0; q < ns; ++q) {
+        const int sidx = adjoint ? ns - 1 - q : q;
+        const DevStage<R>& ds = stages[sidx];
+        if (dp->profile) {
+            dp->ev_stage[q] = sidx;
+            CK(cudaEventRecord(dp->ev[2 * q], s));
+        }
+        // forward: stage sidx reads space sidx-1 (user in for 0) and writes space sidx.
+        VecRef<R> fin = sidx == 0 ? (adjoint ? uout : uin) : internal(sidx - 1);
+        VecRef<R> fout = ds.out_user ? (adjoint ? uin : uout) : internal(sidx);
+        VecRef<R> src = adjoint ? fout : fin;
+        VecRef<R> dst = adjoint ? fin : fout;
+        if (ds.id) {
+            const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
+            // pattern R computes narrow from wide; pattern C wide from narrow.
+            const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
+            if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s);
+            else launch_c<R>(ds, src, dst, nrhs, adjoint, s);
+        } else {
+            launch_s<R>(ds, src, dst, nrhs, adjoint, s);
+        }
+        if (dp->profile) CK(cudaEventRecord(dp->ev[2 * q + 1], s));
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+extern "C" {
+
+int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out) {
+    try {
+        if (!plan || !out) fail(MIDBF_EINVAL, "null argument");
+        if (precision != MIDBF_FP64 && precision != MIDBF_FP32) fail(MIDBF_EINVAL, "unknown precision");
+        if (s_mode != MIDBF_S_ONTHEFLY && s_mode != MIDBF_S_STORED) fail(MIDBF_EINVAL, "unknown middle-factor mode");
+        const Plan& pl = *reinterpret_cast<const Plan*>(plan);
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) fail(MIDBF_ECUDA, "no CUDA device");
+        auto dp = std::make_unique<midbf_dplan>();
+        dp->precision = precision;
+        dp->s_mode = s_mode;
+        CK(cudaGetDevice(&dp->device));
+        dp->nx = pl.nx();
+        dp->nw = pl.nw();
+        if (precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32);
+        else make_stages<double>(dp.get(), pl, dp->st64);
+        dp->launches = precision == MIDBF_FP32 ? count_launches(dp->st32) : count_launches(dp->st64);
+        CK(cudaDeviceSynchronize());
+        *out = dp.release();
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return MIDBF_ENOMEM;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MIDBF_EINTERNAL;
+    }
+}
+
+void midbf_dplan_destroy(midbf_dplan* dp) { delete dp; }
+
+int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes) {
+    if (!dp || !bytes || nrhs <= 0) {
+        set_last_error("midbf_workspace_size: bad argument");
+        return MIDBF_EINVAL;
+    }
+    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+    *bytes = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    return MIDBF_OK;
+}
+
+int midbf_dplan_bytes(const midbf_dplan* dp, size_t* factor_bytes, size_t* index_bytes) {
+    if (!dp) {
+        set_last_error("midbf_dplan_bytes: null plan");
+        return MIDBF_EINVAL;
+    }
+    if (factor_bytes) *factor_bytes = dp->factor_bytes;
+    if (index_bytes) *index_bytes = dp->index_bytes;
+    return MIDBF_OK;
+}
+
+int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches) {
+    (void)nrhs;
+    if (!dp || !launches) {
+        set_last_error("midbf_apply_launches: bad argument");
+        return MIDBF_EINVAL;
+    }
+    *launches = dp->launches;
+    return MIDBF_OK;
+}
+
+int midbf_dplan_profile(midbf_dplan* dp, int enable) {
+    if (!dp) {
+        set_last_error("midbf_dplan_profile: null plan");
+        return MIDBF_EINVAL;
+    }
+    dp->profile = enable != 0;
+    return MIDBF_OK;
+}
+
+int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kinds, double* bytes, int* n_stages) {
+    try {
+        if (!dp || !n_stages || max_stages < 0) fail(MIDBF_EINVAL, "bad argument");
+        if (!dp->profile || dp->ev_stage.empty()) fail(MIDBF_EINVAL, "no profiled apply recorded");
+        const int ns = (int)dp->ev_stage.size();
+        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+        CK(cudaEventSynchronize(dp->ev[2 * ns - 1]));
+        for (int q = 0; q < ns && q < max_stages; ++q) {
+            const int sidx = dp->ev_stage[q];
+            if (ms) CK(cudaEventElapsedTime(&ms[q], dp->ev[2 * q], dp->ev[2 * q + 1]));
+            if (kinds) kinds[q] = dp->stage_kind[sidx];
+            if (bytes)
+                bytes[q] = dp->stage_fixed_bytes[sidx] + (double)dp->stage_vec_entries[sidx] * dp->last_nrhs * (double)ce;
+        }
+        *n_stages = ns;
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, void* out, int64_t ldout,
+                int nrhs, void* stream, void* workspace, size_t workspace_bytes) {
+    try {
+        if (!dp || !in || !out) fail(MIDBF_EINVAL, "null argument");
+        if (nrhs <= 0) fail(MIDBF_EINVAL, "nrhs must be positive");
+        const int64_t nin = adjoint ? dp->nx : dp->nw;
+        const int64_t nout = adjoint ? dp->nw : dp->nx;
+        if (ldin < nin || ldout < nout) fail(MIDBF_EINVAL, "leading dimension smaller than the vector length");
+        size_t need = 0;
+        midbf_workspace_size(dp, nrhs, &need);
+        if (!workspace || workspace_bytes < need) fail(MIDBF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
+        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+        const char* ib = static_cast<const char*>(in);
+        const char* ob = static_cast<const char*>(out);
+        const size_t inb = ((size_t)(nrhs - 1) * ldin + nin) * ce, outb = ((size_t)(nrhs - 1) * ldout + nout) * ce;
+        if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
+        if (dp->nw >= (1LL << 31) || dp->nx >= (1LL << 31)) fail(MIDBF_EINVAL, "vectors longer than 2^31");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
+        else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MIDBF_EINTERNAL;
+    }
+}
+
+int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, void* out_host, int nrhs, void* stream,
+                     void* workspace, size_t workspace_bytes) {
+    try {
+        if (!dp || !in_host || !out_host || nrhs <= 0) fail(MIDBF_EINVAL, "bad argument");
+        size_t need = 0;
+        midbf_workspace_size(dp, nrhs, &need);
+        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+        const int64_t nin = adjoint ? dp->nx : dp->nw;
+        const int64_t nout = adjoint ? dp->nw : dp->nx;
+        const size_t io = (size_t)(nin + nout) * nrhs * ce;
+        if (!workspace || workspace_bytes < need + io) fail(MIDBF_EINVAL, "workspace too small for host I/O");
+        char* base = static_cast<char*>(workspace);
+        char* din = base + need;
+        char* dout = din + (size_t)nin * nrhs * ce;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        CK(cudaMemcpyAsync(din, in_host, (size_t)nin * nrhs * ce, cudaMemcpyHostToDevice, s));
+        int rc = midbf_apply(dp, adjoint, din, nin, dout, nout, nrhs, stream, workspace, need);
+        if (rc != MIDBF_OK) return rc;
+        CK(cudaMemcpyAsync(out_host, dout, (size_t)nout * nrhs * ce, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MIDBF_EINTERNAL;
+    }
+}
+
+}  // extern "C"

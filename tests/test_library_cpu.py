@@ -1,0 +1,207 @@
+"""Host-side checks of the library (no GPU): the C ABI loads and exports every
+declared symbol, the host construction agrees with the oracle and the direct
+sum, the plan file round-trips with the oracle's independent reader/writer,
+and malformed input is rejected with the documented status codes."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct, midbf, planio
+from oracle.phase import Phase as OPhase
+
+mb = pytest.importorskip("paper_1908_09376_gb300")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "midbf.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    names = set(re.findall(r"\b(midbf_[a-z_0-9]+)\s*\(", txt))
+    names -= {"midbf_rows_fn"}
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(mb.LIB_PATH)
+    names = _declared_symbols()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    for n in names:
+        assert n in mb.EXPORTED, f"binding lacks {n}"
+
+
+def _grid(n):
+    X = synth.uniform_grid(n, 2)
+    W = synth.frequency_grid(n, 2)
+    return X, W, (np.zeros(2), 1.0), (np.full(2, -n / 2), float(n))
+
+
+@pytest.mark.parametrize("n,family,n0", [(32, synth.PHASE_FIO2D, 16), (64, synth.PHASE_FIO2D, 64),
+                                         (64, synth.PHASE_FIO2D_JUMP, 64), (32, synth.PHASE_DOT, 4)])
+def test_host_build_matches_direct_sum(n, family, n0):
+    X, W, bx, bw = _grid(n)
+    plan = mb.Plan.build(mb.Phase.closed_form(family, X, W), tol=1e-6, n0=n0, boxX=bx, boxW=bw)
+    fac = planio.read(plan.export())           # applied by the oracle's own code
+    f = synth.complex_gaussian(n * n, 1, 0)[:, 0]
+    g = midbf.apply(fac, f)
+    gd = direct.direct_sum(OPhase(family, X, W), f)
+    assert direct.rel_l2(g, gd) < 2e-5
+    st = plan.stats()
+    assert st["nx"] == n * n and st["nstages"] == 2 * st["nsteps"] + 1
+
+
+def test_host_build_rank_one_exact_and_3d():
+    X, W, bx, bw = _grid(32)
+    for fam in (synth.PHASE_ZERO, synth.PHASE_SEPARABLE):
+        plan = mb.Plan.build(mb.Phase.closed_form(fam, X, W), tol=1e-9, n0=16, boxX=bx, boxW=bw)
+        assert plan.stats()["max_rank"] == 1
+        fac = planio.read(plan.export())
+        f = synth.complex_gaussian(1024, 1, 1)[:, 0]
+        assert direct.rel_l2(midbf.apply(fac, f), direct.direct_sum(OPhase(fam, X, W), f)) < 1e-12
+    n = 8
+    X3 = synth.uniform_random_points(n ** 3, 3, 0)
+    W3 = synth.frequency_grid(n, 3)
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO3D, X3, W3), tol=1e-7, n0=8,
+                         boxX=(np.zeros(3), 1.0), boxW=(np.full(3, -4.0), 8.0))
+    fac = planio.read(plan.export())
+    f = synth.complex_gaussian(n ** 3, 1, 0)[:, 0]
+    assert direct.rel_l2(midbf.apply(fac, f), direct.direct_sum(OPhase(synth.PHASE_FIO3D, X3, W3), f)) < 1e-5
+
+
+def test_lowrank_phase_eval_and_build():
+    n = 32
+    X, W, bx, bw = _grid(n)
+    rng = np.random.default_rng(0)
+    U = np.concatenate([X, rng.standard_normal((n * n, 1)) * 0.01], axis=1)
+    V = np.concatenate([W, rng.standard_normal((n * n, 1))], axis=1)
+    ph = mb.Phase.lowrank(X, W, U, V)
+    ix = np.array([0, 5, 700]); iw = np.array([3, 1000, 17])
+    assert np.allclose(ph.eval(ix, iw), np.sum(U[ix] * V[iw], axis=1), rtol=0, atol=1e-13)
+    U2, V2 = ph.factors()
+    assert np.array_equal(U2, U) and np.array_equal(V2, V)
+    plan = mb.Plan.build(ph, tol=1e-6, n0=16, boxX=bx, boxW=bw)
+    fac = planio.read(plan.export())
+    f = synth.complex_gaussian(n * n, 1, 2)[:, 0]
+    assert direct.rel_l2(midbf.apply(fac, f), direct.direct_sum(fac.phase, f)) < 2e-5
+
+
+def test_phase_eval_matches_hand_values():
+    X = np.array([[0.25, 0.0], [0.5, 0.0]])
+    W = np.array([[3.0, 4.0]])
+    p1 = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    assert abs(p1.eval([0], [0])[0] - 1.375) < 1e-14
+    p3 = mb.Phase.closed_form(synth.PHASE_FIO2D_JUMP, X, W)
+    assert abs(p3.eval([1], [0])[0] - (4 + 13 ** 0.5 / 8)) < 1e-14
+
+
+def test_plan_roundtrip_with_oracle_writer():
+    X, W, bx, bw = _grid(32)
+    fac = midbf.build(OPhase(synth.PHASE_FIO2D, X, W), n0=16, tol=1e-6, t=2.0, boxX=bx, boxW=bw)
+    data = planio.write(fac)
+    plan = mb.Plan.load(data)
+    assert plan.export() == data
+
+
+def test_malformed_input_rejected():
+    X, W, bx, bw = _grid(16)
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Phase.closed_form(synth.PHASE_FIO3D, X, W)
+    assert e.value.code == mb.EINVAL
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Phase.closed_form(99, X, W)
+    assert e.value.code == mb.EINVAL
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16, boxX=bx, boxW=bw)
+    data = bytearray(plan.export())
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Plan.load(bytes(data[:-5]))
+    assert e.value.code == mb.EFORMAT
+    bad = bytearray(data)
+    bad[0:8] = b"XXXXXXXX"
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Plan.load(bytes(bad))
+    assert e.value.code == mb.EFORMAT
+    # an output position written twice must be caught by validation
+    fac = planio.read(bytes(data))
+    st = fac.stages[0]
+    st.blocks[1].out_idx = st.blocks[0].out_idx.copy()
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Plan.load(planio.write(fac))
+    assert e.value.code == mb.EFORMAT
+
+
+def test_apply_without_gpu_fails_loudly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    X, W, bx, bw = _grid(16)
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16, boxX=bx, boxW=bw)
+    with pytest.raises(mb.MidbfError) as e:
+        mb.DevicePlan(plan, mb.FP32)
+    assert e.value.code == mb.ECUDA
+
+
+def _access(P, n):
+    rows = lambda idx: np.exp(2j * np.pi * P(idx[:, None], np.arange(n)[None, :]))
+    cols = lambda idx: np.exp(2j * np.pi * P(np.arange(n)[:, None], idx[None, :]))
+    return rows, cols
+
+
+def test_recovery_exact_for_smooth_phase():
+    """Algorithm 7 through the C ABI: small path increments -> exact low-rank phase."""
+    from oracle import recovery
+    n = 32
+    X = synth.uniform_grid(n, 2) * 0.3
+    W = synth.frequency_grid(n, 2)
+    P = OPhase(synth.PHASE_DOT, X, W)
+    rows, cols = _access(P, n * n)
+    ph = mb.Phase.recover(X, W, rows, cols, r=4, q=2, seed=1)
+    info = ph.info
+    assert info["mismatches"] == 0 and info["disc_rows"] == 0 and info["disc_cols"] == 0
+    assert info["tau"] == 0.25 and info["rows_requested"] >= 8 and info["cols_requested"] >= 8
+    U, V = ph.factors()
+    S = synth.sample_rows(n * n, 200, 3)
+    assert recovery.eps_K(P, U, V, S) < 1e-9
+
+
+def test_recovery_3d_random_points():
+    from oracle import recovery
+    X = synth.uniform_random_points(600, 3, 4) * 0.25
+    W = synth.uniform_random_points(600, 3, 5) * 2.0
+    P = OPhase(synth.PHASE_DOT, X, W)
+    rows, cols = _access(P, 600)
+    ph = mb.Phase.recover(X, W, rows, cols, r=5, q=2, seed=2)
+    U, V = ph.factors()
+    assert ph.info["mismatches"] == 0
+    assert recovery.eps_K(P, U, V, synth.sample_rows(600, 150, 1)) < 1e-9
+
+
+def test_recovery_reports_aliasing_on_nyquist_grid():
+    """On the uniform FIO grids the phase changes by more than 1/2 per grid
+    step near the Nyquist frequency, outside Lemma 3.2's hypothesis: tau is
+    driven to 1/2 and recovered rows and columns disagree.  The library must
+    report this rather than hide it (the oracle sees the same)."""
+    n = 32
+    X = synth.uniform_grid(n, 2)
+    W = synth.frequency_grid(n, 2)
+    P = OPhase(synth.PHASE_FIO2D, X, W)
+    rows, cols = _access(P, n * n)
+    ph = mb.Phase.recover(X, W, rows, cols, r=4, q=2, seed=0)
+    assert ph.info["tau"] == 0.5 and ph.info["mismatches"] > 0
+
+
+def test_recovery_callback_failure():
+    X = synth.uniform_grid(8, 2)
+    W = synth.frequency_grid(8, 2)
+
+    def bad(idx):
+        raise RuntimeError("no access")
+
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Phase.recover(X, W, bad, bad, r=2, q=2)
+    assert e.value.code == mb.ECALLBACK
