@@ -243,7 +243,10 @@ class Plan:
         n = C.c_size_t()
         check(midbf_plan_export(self.h, C.byref(buf), C.byref(n)), "midbf_plan_export")
         try:
-            return C.string_at(buf, n.value)
+            if n.value == 0:
+                return b""
+            arr = np.ctypeslib.as_array(C.cast(buf, C.POINTER(C.c_uint8)), shape=(n.value,))
+            return arr.tobytes()
         finally:
             midbf_free(buf)
 

@@ -11,6 +11,7 @@
 // conjugated factors (adjoint), ping-ponging between two workspace vectors.
 #include <algorithm>
 #include <cstdio>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -30,6 +31,7 @@ namespace {
     } while (0)
 
 constexpr int kRangeC = 64;   // output entries per pattern-C item
+constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory budget per CTA
 
 struct DevBuf {
     void* p = nullptr;
@@ -48,14 +50,13 @@ struct DevStage : DevStageBase {
     bool id = false;
     IdStage<R> ids{};
     int n_items_r = 0, n_items_c = 0, rt = 1;
-    size_t smem_r = 0, smem_c = 0;
+    int max_nred = 0, max_narrow = 0, max_nsub = 1;
     // on-the-fly S
     SStage<R> ss{};
     SSide<R> srows{}, scols{};
     const int2* items_rows = nullptr;
     const int2* items_cols = nullptr;
     int n_items_rows = 0, n_items_cols = 0, rt_rows = 1, rt_cols = 1;
-    size_t smem_rows = 0, smem_cols = 0;
 };
 
 }  // namespace
@@ -199,9 +200,11 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     ds.rt = rt;
     ds.n_items_r = (int)items_r.size();
     ds.n_items_c = (int)items_c.size();
-    ds.smem_r = (max_nred + (size_t)kWarps * 32 * rt) * sizeof(cx<R>);
-    ds.smem_c = (max_narrow + max_nsub * kRangeC) * sizeof(cx<R>);
-    if (ds.smem_r > 200 * 1024 || ds.smem_c > 200 * 1024) fail(MIDBF_EINTERNAL, "block too wide for shared memory");
+    ds.max_nred = (int)max_nred;
+    ds.max_narrow = (int)max_narrow;
+    ds.max_nsub = (int)max_nsub;
+    if (pattern_r_smem<R>((int)max_nred, rt, 1) > kSmemCap || pattern_c_smem<R>((int)max_narrow, (int)max_nsub, kRangeC, 1) > kSmemCap)
+        fail(MIDBF_EINTERNAL, "block too wide for shared memory");
     ds.ids.subs = upload(dp, subs, &dp->index_bytes);
     ds.ids.blocks = upload(dp, blocks, &dp->index_bytes);
     ds.ids.skel = upload(dp, skel, &dp->index_bytes);
@@ -348,8 +351,8 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
         for (int64_t v : bk.out_idx) rpos.push_back((int)v);
         for (int64_t v : bk.in_idx) cpos.push_back((int)v);
     }
-    ds.rt_rows = rows_per_lane(maxr);
-    ds.rt_cols = rows_per_lane(maxc);
+    ds.rt_rows = 2;  // k_s_fly launches use 64 rows per item
+    ds.rt_cols = 2;
     for (size_t b = 0; b < st.blocks.size(); ++b) {
         for (int r0 = 0; r0 < blk_nrow[b]; r0 += 32 * ds.rt_rows) it_rows.push_back(make_int2((int)b, r0));
         for (int c0 = 0; c0 < blk_ncol[b]; c0 += 32 * ds.rt_cols) it_cols.push_back(make_int2((int)b, c0));
@@ -372,8 +375,6 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     ds.items_cols = upload(dp, it_cols, &dp->index_bytes);
     ds.n_items_rows = (int)it_rows.size();
     ds.n_items_cols = (int)it_cols.size();
-    ds.smem_rows = s_fly_smem<R>(P, Q, ds.rt_rows);
-    ds.smem_cols = s_fly_smem<R>(P, Q, ds.rt_cols);
 }
 
 template <class R>
@@ -411,63 +412,116 @@ void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
+// Right-hand sides per kernel pass: the smallest tile that covers nrhs (at
+// most 16 for FP32, 8 for FP64), halved while the shared-memory need is
+// above the budget.
+template <class R>
+int pick_nr(int nrhs, const std::function<size_t(int)>& smem) {
+    const int cap = sizeof(R) == 4 ? 16 : 8;
+    int nr = 1;
+    while (nr < nrhs && nr < cap) nr *= 2;
+    while (nr > 1 && smem(nr) > kSmemCap) nr /= 2;
+    return nr;
+}
+
+template <class R, int RT, int NR, bool CJ>
+void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+    const size_t sm = pattern_r_smem<R>(ds.max_nred, RT, NR);
+    auto kf = k_pattern_r<R, RT, NR, CJ>;
+    set_smem(kf, sm);
+    kf<<<ds.n_items_r, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+}
+
+template <class R, int RT, bool CJ>
+void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+    switch (nr) {
+        case 1: launch_r_t<R, RT, 1, CJ>(ds, src, dst, nrhs, s); break;
+        case 2: launch_r_t<R, RT, 2, CJ>(ds, src, dst, nrhs, s); break;
+        case 4: launch_r_t<R, RT, 4, CJ>(ds, src, dst, nrhs, s); break;
+        case 8: launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s); break;
+        default:
+            if constexpr (sizeof(R) == 4) launch_r_t<R, RT, 16, CJ>(ds, src, dst, nrhs, s);
+            else launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s);
+    }
+}
+
 template <class R>
 void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
     if (ds.n_items_r == 0) return;
-#define LR(RT, CJ)                                                                                   \
-    {                                                                                                \
-        auto kf = k_pattern_r<R, RT, CJ>;                                                            \
-        set_smem(kf, ds.smem_r);                                                                     \
-        kf<<<ds.n_items_r, kThreads, ds.smem_r, s>>>(ds.ids, src, dst, nrhs);                        \
-    }
+    const int nr = pick_nr<R>(nrhs, [&](int q) { return pattern_r_smem<R>(ds.max_nred, ds.rt, q); });
     if (ds.rt == 1) {
-        if (conj) LR(1, true) else LR(1, false)
+        if (conj) launch_r_nr<R, 1, true>(ds, src, dst, nrhs, nr, s);
+        else launch_r_nr<R, 1, false>(ds, src, dst, nrhs, nr, s);
     } else {
-        if (conj) LR(2, true) else LR(2, false)
+        if (conj) launch_r_nr<R, 2, true>(ds, src, dst, nrhs, nr, s);
+        else launch_r_nr<R, 2, false>(ds, src, dst, nrhs, nr, s);
     }
-#undef LR
     CK(cudaGetLastError());
+}
+
+template <class R, int NR, bool CJ>
+void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+    const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, NR);
+    auto kf = k_pattern_c<R, NR, CJ>;
+    set_smem(kf, sm);
+    kf<<<ds.n_items_c, kThreads, sm, s>>>(ds.ids, src, dst, nrhs, kRangeC);
+}
+
+template <class R, bool CJ>
+void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+    switch (nr) {
+        case 1: launch_c_t<R, 1, CJ>(ds, src, dst, nrhs, s); break;
+        case 2: launch_c_t<R, 2, CJ>(ds, src, dst, nrhs, s); break;
+        case 4: launch_c_t<R, 4, CJ>(ds, src, dst, nrhs, s); break;
+        case 8: launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s); break;
+        default:
+            if constexpr (sizeof(R) == 4) launch_c_t<R, 16, CJ>(ds, src, dst, nrhs, s);
+            else launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s);
+    }
 }
 
 template <class R>
 void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
     if (ds.n_items_c == 0) return;
-    if (conj) {
-        auto kf = k_pattern_c<R, true>;
-        set_smem(kf, ds.smem_c);
-        kf<<<ds.n_items_c, kThreads, ds.smem_c, s>>>(ds.ids, src, dst, nrhs, kRangeC);
-    } else {
-        auto kf = k_pattern_c<R, false>;
-        set_smem(kf, ds.smem_c);
-        kf<<<ds.n_items_c, kThreads, ds.smem_c, s>>>(ds.ids, src, dst, nrhs, kRangeC);
-    }
+    const int nr = pick_nr<R>(nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
+    if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s);
+    else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s);
     CK(cudaGetLastError());
+}
+
+template <class R, int RT, int NR, bool CJ>
+void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+    SStage<R> st = ds.ss;
+    const size_t sm = s_fly_smem<R>(st.P, st.Q, RT, NR);
+    auto kf = k_s_fly<R, RT, NR, CJ>;
+    set_smem(kf, sm);
+    if (!CJ) {
+        st.items = ds.items_rows;
+        kf<<<ds.n_items_rows, kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs);
+    } else {
+        st.items = ds.items_cols;
+        kf<<<ds.n_items_cols, kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs);
+    }
+}
+
+template <class R, bool CJ>
+void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+    switch (nr) {
+        case 1: launch_s_t<R, 2, 1, CJ>(ds, src, dst, nrhs, s); break;
+        case 2: launch_s_t<R, 2, 2, CJ>(ds, src, dst, nrhs, s); break;
+        case 4: launch_s_t<R, 2, 4, CJ>(ds, src, dst, nrhs, s); break;
+        case 8: launch_s_t<R, 2, 8, CJ>(ds, src, dst, nrhs, s); break;
+        default:
+            if constexpr (sizeof(R) == 4) launch_s_t<R, 2, 16, CJ>(ds, src, dst, nrhs, s);
+            else launch_s_t<R, 2, 8, CJ>(ds, src, dst, nrhs, s);
+    }
 }
 
 template <class R>
 void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s) {
-    SStage<R> st = ds.ss;
-    if (!adjoint) {
-        st.items = ds.items_rows;
-#define LS(RT)                                                                                         \
-    {                                                                                                  \
-        auto kf = k_s_fly<R, RT, false>;                                                               \
-        set_smem(kf, ds.smem_rows);                                                                    \
-        kf<<<ds.n_items_rows, kThreads, ds.smem_rows, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs); \
-    }
-        if (ds.rt_rows == 1) LS(1) else LS(2)
-#undef LS
-    } else {
-        st.items = ds.items_cols;
-#define LS(RT)                                                                                         \
-    {                                                                                                  \
-        auto kf = k_s_fly<R, RT, true>;                                                                \
-        set_smem(kf, ds.smem_cols);                                                                    \
-        kf<<<ds.n_items_cols, kThreads, ds.smem_cols, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs); \
-    }
-        if (ds.rt_cols == 1) LS(1) else LS(2)
-#undef LS
-    }
+    const int nr = pick_nr<R>(nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, 2, q); });
+    if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s);
+    else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s);
     CK(cudaGetLastError());
 }
 
