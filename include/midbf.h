@@ -229,6 +229,30 @@ int midbf_dplan_profile(midbf_dplan* dp, int enable);
 int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kinds, double* bytes,
                       int* n_stages);
 
+/* midbf_apply_noalloc: midbf_apply for callers that cannot allocate device
+ * memory when they apply the operator - for example a service whose GPU
+ * memory is entirely owned by another allocator, or a latency-bound loop in
+ * which cudaMalloc would synchronize the device.  It takes no workspace:
+ * the intermediate vectors live in one scratch array of
+ * midbf_noalloc_scratch_bytes() bytes (32 MiB) that the library holds in the
+ * device memory of every GPU that loads it, until the process exits.  It
+ * calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - Arguments and layout are those of midbf_apply; dp's device must be the
+ *     current device.
+ *   - Plans whose workspace for nrhs right-hand sides (midbf_workspace_size)
+ *     exceeds the scratch size are rejected with MIDBF_EINVAL and a message
+ *     saying how many bytes they need.
+ *   - The first call on a device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the array and a call overwrites the previous call's
+ *     contents; calls that overlap on the GPU (different streams, unordered
+ *     host threads) race on it and give wrong results.
+ * The paper has no counterpart to this call: it is an allocation policy of
+ * this library, not a step of the method. */
+int midbf_apply_noalloc(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin,
+                        void* out, int64_t ldout, int nrhs, void* stream);
+size_t midbf_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

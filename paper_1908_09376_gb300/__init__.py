@@ -94,6 +94,9 @@ midbf_apply_launches = _sig("midbf_apply_launches", C.c_int, [_vp, C.c_int, C.PO
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
+midbf_apply_noalloc = _sig("midbf_apply_noalloc", C.c_int,
+                           [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp])
+midbf_noalloc_scratch_bytes = _sig("midbf_noalloc_scratch_bytes", C.c_size_t, [])
 
 EXPORTED = [n for n in dir() if n.startswith("midbf_") and callable(globals()[n])
             and not isinstance(globals()[n], type)]

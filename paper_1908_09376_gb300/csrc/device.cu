@@ -737,3 +737,89 @@ int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, vo
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Apply without any allocation.
+//
+// Some callers cannot allocate device memory at the time they apply the
+// operator: a service whose GPU memory is entirely owned by another allocator
+// (a framework's caching allocator, a fixed memory pool), or a latency-bound
+// loop where cudaMalloc would synchronize the device and stall other work.
+// midbf_apply_noalloc serves them: instead of a caller workspace it uses one
+// statically sized scratch array in device memory that every GPU loading this
+// library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+// allocating library routine.
+//
+// The array is shared by all calls: a call overwrites what the previous call
+// left there (the kernels write every scratch entry they read, so nothing has
+// to start at zero), and calls that overlap on the GPU - on different streams,
+// or from different host threads without ordering - race on it.
+namespace {
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+}
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};  // device address of the scratch array, per device
+
+// Device address of the scratch array on the current device.  The host-side
+// name g_noalloc_scratch is only a stand-in, never a device address, so the
+// address is looked up once per device with that device current.
+void* noalloc_scratch(int dev) {
+    if (dev < 0 || dev >= 256) fail(MIDBF_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            fail(MIDBF_ECUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+extern "C" {
+
+size_t midbf_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
+
+int midbf_apply_noalloc(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, void* out, int64_t ldout,
+                        int nrhs, void* stream) {
+    try {
+        if (!dp || !in || !out) fail(MIDBF_EINVAL, "null argument");
+        if (nrhs <= 0) fail(MIDBF_EINVAL, "nrhs must be positive");
+        const int64_t nin = adjoint ? dp->nx : dp->nw;
+        const int64_t nout = adjoint ? dp->nw : dp->nx;
+        if (ldin < nin || ldout < nout) fail(MIDBF_EINVAL, "leading dimension smaller than the vector length");
+        size_t need = 0;
+        midbf_workspace_size(dp, nrhs, &need);
+        if (need > kNoAllocScratchBytes)
+            fail(MIDBF_EINVAL, "midbf_apply_noalloc: this plan needs " + std::to_string(need) +
+                                   " bytes of scratch for " + std::to_string(nrhs) +
+                                   " right-hand sides, more than the built-in " +
+                                   std::to_string(kNoAllocScratchBytes) +
+                                   " bytes; use midbf_apply with a caller workspace or fewer right-hand sides");
+        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+        const char* ib = static_cast<const char*>(in);
+        const char* ob = static_cast<const char*>(out);
+        const size_t inb = ((size_t)(nrhs - 1) * ldin + nin) * ce, outb = ((size_t)(nrhs - 1) * ldout + nout) * ce;
+        if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        if (dev != dp->device) fail(MIDBF_EINVAL, "the current device is not the device of this plan");
+        void* scratch = noalloc_scratch(dev);
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, scratch);
+        else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, scratch);
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MIDBF_EINTERNAL;
+    }
+}
+
+}  // extern "C"
