@@ -57,6 +57,22 @@ def dist_setup():
     return ws, rank, local
 
 
+def aggregate(total_ms_local, units_per_step_per_rank, steps, pg=None, device=None):
+    """Whole-job throughput of `steps` timed steps on every rank: the slowest
+    rank's time defines the step time (max over ranks); every rank processed
+    its own replica, so the units add up over ranks."""
+    total_ms = float(total_ms_local)
+    world = 1
+    if pg is not None:
+        import torch
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        total_ms = tt.item()
+        world = pg.get_world_size()
+    ms_per_step = total_ms / steps
+    return ms_per_step, world * units_per_step_per_rank / (ms_per_step * 1e-3)
+
+
 def workload(n):
     X = synth.uniform_grid(n, 2)
     W = synth.frequency_grid(n, 2)
@@ -261,13 +277,7 @@ def main():
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
-    total_ms = sum(step_ms)
-    if pg:
-        tt = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
-        total_ms = tt.item()
-    ms_per_step = total_ms / args.steps
-    value = ws * 2 * N / (ms_per_step * 1e-3)
+    ms_per_step, value = aggregate(sum(step_ms), 2 * N, args.steps, pg, dev)
 
     # the same steps again with CUDA events around every stage launch
     dp32.profile(True)

@@ -49,7 +49,8 @@ struct DevStage : DevStageBase {
     // ID stages (and stored S)
     bool id = false;
     IdStage<R> ids{};
-    int n_items_r = 0, n_items_c = 0, rt = 1;
+    IdStage<R> ids1{};   // same data, items for the one-RHS pattern-C kernel
+    int n_items_r = 0, n_items_c = 0, n_items_c1 = 0, rt = 1;
     int max_nred = 0, max_narrow = 0, max_nsub = 1;
     // on-the-fly S
     SStage<R> ss{};
@@ -114,7 +115,7 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     std::vector<BlockDesc> blocks;
     std::vector<int> skel, red, wide_pos, narrow_pos;
     std::vector<ItemR> items_r;
-    std::vector<ItemC> items_c;
+    std::vector<ItemC> items_c, items_c1;
     std::vector<cx<R>> T;
     int maxk = 1;
     size_t max_nred = 0, max_narrow = 0, max_nsub = 1;
@@ -191,6 +192,7 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
         max_narrow = std::max(max_narrow, (size_t)bd.nnarrow);
         blocks.push_back(bd);
         for (int o0 = 0; o0 < bd.m; o0 += kRangeC) items_c.push_back({(int)b, o0, std::min(bd.m, o0 + kRangeC), 0});
+        for (int o0 = 0; o0 < bd.m; o0 += kRangeC1) items_c1.push_back({(int)b, o0, std::min(bd.m, o0 + kRangeC1), 0});
     }
     if (max_nsub > 16) fail(MIDBF_EINTERNAL, "more than 16 sub-blocks in a block");
     const int rt = rows_per_lane(maxk);
@@ -214,6 +216,9 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     ds.ids.T = upload(dp, T, &dp->factor_bytes);
     ds.ids.items_r = upload(dp, items_r, &dp->index_bytes);
     ds.ids.items_c = upload(dp, items_c, &dp->index_bytes);
+    ds.ids1 = ds.ids;
+    ds.ids1.items_c = upload(dp, items_c1, &dp->index_bytes);
+    ds.n_items_c1 = (int)items_c1.size();
 }
 
 // Split of the phase for one S block (see kernels.cuh): rows get (a, u, C),
@@ -483,6 +488,22 @@ void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, 
 template <class R>
 void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
     if (ds.n_items_c == 0) return;
+    if (nrhs == 1) {
+        const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
+        if (sm <= kSmemCap) {
+            if (conj) {
+                auto kf = k_pattern_c1<R, true>;
+                set_smem(kf, sm);
+                kf<<<ds.n_items_c1, kThreads, sm, s>>>(ds.ids1, src, dst);
+            } else {
+                auto kf = k_pattern_c1<R, false>;
+                set_smem(kf, sm);
+                kf<<<ds.n_items_c1, kThreads, sm, s>>>(ds.ids1, src, dst);
+            }
+            CK(cudaGetLastError());
+            return;
+        }
+    }
     const int nr = pick_nr<R>(nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
     if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s);
     else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s);

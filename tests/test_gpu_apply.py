@@ -95,7 +95,7 @@ def test_apply_matches_oracle_on_oracle_plans(case, prec, s_mode):
     fac, plan, mats = oracle_case(case)
     dp = mb.DevicePlan(plan, prec, s_mode)
     dev = torch.device("cuda:0")
-    for nrhs in (1, 3):
+    for nrhs in (1, 3, 20):
         f = synth.complex_gaussian(fac.nw, nrhs, 11)
         h = synth.complex_gaussian(fac.nx, nrhs, 12)
         g = dp.apply(torch.from_numpy(f.T.copy()).to(dev, _dt(prec))).cpu().numpy().T
