@@ -215,6 +215,23 @@ int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin
 int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, void* out_host,
                      int nrhs, void* stream, void* workspace, size_t workspace_bytes);
 
+/* ---- batched apply (many uneven instances) -------------------------------
+ * midbf_apply_batched: count independent applies of possibly different plans,
+ * directions (adjoint[i]) and numbers of right-hand sides (nrhs[i]), issued
+ * together on one stream.  Level index q of every instance goes into one
+ * group of launches (forward instances run their stage q, adjoint instances
+ * their stage ns-1-q), so the number of launches grows with the number of
+ * levels and kernel variants, not with count.  All dplans must share one
+ * precision and device; in[i]/out[i] are device vectors with leading
+ * dimensions ldin[i]/ldout[i] as in midbf_apply; no two instances may share
+ * an output.  workspace: device memory of midbf_batched_workspace_size bytes.
+ * Errors: MIDBF_EINVAL, MIDBF_ECUDA. */
+int midbf_batched_workspace_size(int count, const midbf_dplan* const* dps, const int* nrhs, size_t* bytes);
+int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adjoint,
+                        const void* const* in, const int64_t* ldin, void* const* out,
+                        const int64_t* ldout, const int* nrhs, void* stream,
+                        void* workspace, size_t workspace_bytes);
+
 /* Number of kernel launches one midbf_apply issues (for launch accounting). */
 int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches);
 

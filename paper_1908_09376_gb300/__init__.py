@@ -94,6 +94,11 @@ midbf_apply_launches = _sig("midbf_apply_launches", C.c_int, [_vp, C.c_int, C.PO
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
+midbf_batched_workspace_size = _sig("midbf_batched_workspace_size", C.c_int,
+                                    [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_size_t)])
+midbf_apply_batched = _sig("midbf_apply_batched", C.c_int,
+                           [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_vp), _i64p, C.POINTER(_vp),
+                            _i64p, C.POINTER(C.c_int), _vp, _vp, C.c_size_t])
 midbf_apply_noalloc = _sig("midbf_apply_noalloc", C.c_int,
                            [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp])
 midbf_noalloc_scratch_bytes = _sig("midbf_noalloc_scratch_bytes", C.c_size_t, [])
@@ -346,6 +351,33 @@ class DevicePlan:
         check(midbf_apply_host(self.h, int(adjoint), xs.ctypes.data, out.ctypes.data, nrhs, s.cuda_stream,
                                workspace.data_ptr(), workspace.numel()), "midbf_apply_host")
         return out.reshape(-1) if vec else out
+
+
+def apply_batched(dplans, xs, adjoints, outs=None, workspace=None, stream=None):
+    """Batched apply through midbf_apply_batched.  xs[i]: CUDA tensor (nrhs_i, n_in_i)
+    (one RHS per row); returns the outputs (nrhs_i, n_out_i)."""
+    import torch
+    n = len(dplans)
+    xs = [x.reshape(1, -1) if x.dim() == 1 else x for x in xs]
+    xs = [x.contiguous() for x in xs]
+    nrhs = (C.c_int * n)(*[x.shape[0] for x in xs])
+    adj = (C.c_int * n)(*[int(a) for a in adjoints])
+    hs = (_vp * n)(*[d.h.value for d in dplans])
+    if outs is None:
+        outs = [torch.empty((x.shape[0], d.nw if a else d.nx), dtype=x.dtype, device=x.device)
+                for d, x, a in zip(dplans, xs, adjoints)]
+    ins = (_vp * n)(*[x.data_ptr() for x in xs])
+    ots = (_vp * n)(*[o.data_ptr() for o in outs])
+    ldi = (C.c_int64 * n)(*[x.shape[1] for x in xs])
+    ldo = (C.c_int64 * n)(*[o.shape[1] for o in outs])
+    need = C.c_size_t()
+    check(midbf_batched_workspace_size(n, hs, nrhs, C.byref(need)), "midbf_batched_workspace_size")
+    if workspace is None:
+        workspace = torch.empty(need.value, dtype=torch.uint8, device=xs[0].device)
+    s = torch.cuda.current_stream(xs[0].device) if stream is None else stream
+    check(midbf_apply_batched(n, hs, adj, ins, ldi, ots, ldo, nrhs, s.cuda_stream, workspace.data_ptr(),
+                              workspace.numel()), "midbf_apply_batched")
+    return outs
 
 
 def _autograd():

@@ -13,6 +13,10 @@
 #include <cstdio>
 #include <functional>
 #include <mutex>
+#include <array>
+#include <map>
+#include <set>
+#include <type_traits>
 #include <numeric>
 #include <thread>
 
@@ -55,9 +59,11 @@ struct DevStage : DevStageBase {
     // on-the-fly S
     SStage<R> ss{};
     SSide<R> srows{}, scols{};
-    const int2* items_rows = nullptr;
+    const int2* items_rows = nullptr;   // 64-row items (RT = 2)
     const int2* items_cols = nullptr;
-    int n_items_rows = 0, n_items_cols = 0, rt_rows = 1, rt_cols = 1;
+    const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
+    const int2* items_cols4 = nullptr;
+    int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
 };
 
 }  // namespace
@@ -335,7 +341,7 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     if (P > 8 || Q > 3) fail(MIDBF_EINVAL, "on-the-fly middle factor supports at most 8 low-rank terms");
     std::vector<int> blk_rows, blk_cols, blk_nrow, blk_ncol, rpos, cpos;
     std::vector<R> ra, ru, rc, ca, cu, cc;
-    std::vector<int2> it_rows, it_cols;
+    std::vector<int2> it_rows, it_cols, it_rows4, it_cols4;
     int maxr = 1, maxc = 1;
     for (size_t b = 0; b < st.blocks.size(); ++b) {
         const Block& bk = st.blocks[b];
@@ -361,6 +367,8 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     for (size_t b = 0; b < st.blocks.size(); ++b) {
         for (int r0 = 0; r0 < blk_nrow[b]; r0 += 32 * ds.rt_rows) it_rows.push_back(make_int2((int)b, r0));
         for (int c0 = 0; c0 < blk_ncol[b]; c0 += 32 * ds.rt_cols) it_cols.push_back(make_int2((int)b, c0));
+        for (int r0 = 0; r0 < blk_nrow[b]; r0 += 128) it_rows4.push_back(make_int2((int)b, r0));
+        for (int c0 = 0; c0 < blk_ncol[b]; c0 += 128) it_cols4.push_back(make_int2((int)b, c0));
     }
     ds.ss.P = P;
     ds.ss.Q = Q;
@@ -378,8 +386,12 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     ds.scols.pos = upload(dp, cpos, &dp->index_bytes);
     ds.items_rows = upload(dp, it_rows, &dp->index_bytes);
     ds.items_cols = upload(dp, it_cols, &dp->index_bytes);
+    ds.items_rows4 = upload(dp, it_rows4, &dp->index_bytes);
+    ds.items_cols4 = upload(dp, it_cols4, &dp->index_bytes);
     ds.n_items_rows = (int)it_rows.size();
     ds.n_items_cols = (int)it_cols.size();
+    ds.n_items_rows4 = (int)it_rows4.size();
+    ds.n_items_cols4 = (int)it_cols4.size();
 }
 
 template <class R>
@@ -412,9 +424,23 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out)
     }
 }
 
+// Raise a kernel's dynamic shared-memory limit to the library's cap, once per
+// kernel and device, so apply calls issue no attribute calls afterwards.
+void set_smem_ptr(const void* kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return;
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    if (done.count({kernel, dev})) return;
+    CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+    done.insert({kernel, dev});
+}
+
 template <class K>
 void set_smem(K kernel, size_t bytes) {
-    if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    set_smem_ptr(reinterpret_cast<const void*>(kernel), bytes);
 }
 
 // Right-hand sides per kernel pass: the smallest tile that covers nrhs (at
@@ -469,7 +495,7 @@ void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
     const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, NR);
     auto kf = k_pattern_c<R, NR, CJ>;
     set_smem(kf, sm);
-    kf<<<ds.n_items_c, kThreads, sm, s>>>(ds.ids, src, dst, nrhs, kRangeC);
+    kf<<<ds.n_items_c, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
 }
 
 template <class R, bool CJ>
@@ -510,37 +536,60 @@ void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
     CK(cudaGetLastError());
 }
 
-template <class R, int RT, int NR, bool CJ>
+template <class R, int RT, int NR, bool CJ, int PQ>
 void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
     SStage<R> st = ds.ss;
     const size_t sm = s_fly_smem<R>(st.P, st.Q, RT, NR);
-    auto kf = k_s_fly<R, RT, NR, CJ>;
+    auto kf = k_s_fly<R, RT, NR, CJ, PQ>;
     set_smem(kf, sm);
+    const bool four = RT == 4;
     if (!CJ) {
-        st.items = ds.items_rows;
-        kf<<<ds.n_items_rows, kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs);
+        st.items = four ? ds.items_rows4 : ds.items_rows;
+        kf<<<four ? ds.n_items_rows4 : ds.n_items_rows, kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs);
     } else {
-        st.items = ds.items_cols;
-        kf<<<ds.n_items_cols, kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs);
+        st.items = four ? ds.items_cols4 : ds.items_cols;
+        kf<<<four ? ds.n_items_cols4 : ds.n_items_cols, kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs);
+    }
+}
+
+// FP32: 128-row items for up to 4 RHS per pass, phase shape fixed at compile
+// time for the workload families.  FP64: the general shape (the plain form
+// stores the middle factor by default).
+template <class R, bool CJ, int PQ>
+void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        switch (nr) {
+            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s); break;
+            case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s); break;
+            case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s); break;
+            case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s); break;
+            default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s);
+        }
+    } else {
+        switch (nr) {
+            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s); break;
+            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s); break;
+            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s); break;
+            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s);
+        }
     }
 }
 
 template <class R, bool CJ>
 void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
-    switch (nr) {
-        case 1: launch_s_t<R, 2, 1, CJ>(ds, src, dst, nrhs, s); break;
-        case 2: launch_s_t<R, 2, 2, CJ>(ds, src, dst, nrhs, s); break;
-        case 4: launch_s_t<R, 2, 4, CJ>(ds, src, dst, nrhs, s); break;
-        case 8: launch_s_t<R, 2, 8, CJ>(ds, src, dst, nrhs, s); break;
-        default:
-            if constexpr (sizeof(R) == 4) launch_s_t<R, 2, 16, CJ>(ds, src, dst, nrhs, s);
-            else launch_s_t<R, 2, 8, CJ>(ds, src, dst, nrhs, s);
+    switch (sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0) {
+        case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s); break;
+        case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s); break;
+        case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s); break;
+        case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s); break;
+        case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s); break;
+        default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s);
     }
 }
 
 template <class R>
 void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s) {
-    const int nr = pick_nr<R>(nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, 2, q); });
+    const int nr = pick_nr<R>(nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
     if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s);
     else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s);
     CK(cudaGetLastError());
@@ -593,6 +642,219 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
             launch_s<R>(ds, src, dst, nrhs, adjoint, s);
         }
         if (dp->profile) CK(cudaEventRecord(dp->ev[2 * q + 1], s));
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched apply: level index q of every instance in one group of launches.
+// Forward instances run their stage q, adjoint instances their stage ns-1-q;
+// instances are grouped by kernel variant (pattern, rows per lane, RHS tile,
+// phase shape) and up to kBatch instances share a launch.
+template <class R>
+const std::vector<DevStage<R>>& stages_of(const midbf_dplan* dp);
+template <>
+const std::vector<DevStage<float>>& stages_of<float>(const midbf_dplan* dp) { return dp->st32; }
+template <>
+const std::vector<DevStage<double>>& stages_of<double>(const midbf_dplan* dp) { return dp->st64; }
+
+size_t instance_workspace(const midbf_dplan* dp, int nrhs) {
+    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    return (b + 255) / 256 * 256;
+}
+
+enum { BT_R = 0, BT_C = 1, BT_C1 = 2, BT_S = 3 };
+
+template <class R, class E>
+void launch_batch_group(const midbf_dplan* const* dps, const std::array<int, 4>& key, const E* ents, int n,
+                        const int* nrhs, const int* adjoint, cudaStream_t s) {
+    const int type = key[0], rt = key[1], nr = key[2], pq = key[3];
+    if (type == BT_S) {
+        BatchS<R> a{};
+        a.ninst = n;
+        size_t sm = 0;
+        int items = 0;
+        for (int k = 0; k < n; ++k) {
+            const E& e = ents[k];
+            const DevStage<R>& ds = stages_of<R>(dps[e.i])[e.sidx];
+            const bool adj = adjoint[e.i] != 0;
+            a.st[k] = ds.ss;
+            const bool four = rt == 4;
+            a.st[k].items = adj ? (four ? ds.items_cols4 : ds.items_cols) : (four ? ds.items_rows4 : ds.items_rows);
+            a.rs[k] = adj ? ds.scols : ds.srows;
+            a.cs[k] = adj ? ds.srows : ds.scols;
+            a.src[k] = e.src;
+            a.dst[k] = e.dst;
+            a.nrhs[k] = nrhs[e.i];
+            a.conj[k] = adj;
+            a.item0[k] = items;
+            items += adj ? (four ? ds.n_items_cols4 : ds.n_items_cols) : (four ? ds.n_items_rows4 : ds.n_items_rows);
+            sm = std::max(sm, s_fly_smem<R>(ds.ss.P, ds.ss.Q, rt, nr));
+        }
+        a.item0[n] = items;
+        if (items == 0) return;
+#define LB(RT_, NR_, PQ_)                                        \
+    {                                                            \
+        auto kf = k_batch_s<R, RT_, NR_, PQ_>;                   \
+        set_smem(kf, sm);                                        \
+        kf<<<items, kThreads, sm, s>>>(a);                       \
+    }
+        if constexpr (sizeof(R) == 4) {
+            auto go = [&](auto pqc) {
+                constexpr int P_ = decltype(pqc)::value;
+                switch (nr) {
+                    case 1: LB(4, 1, P_) break;
+                    case 2: LB(4, 2, P_) break;
+                    case 4: LB(4, 4, P_) break;
+                    case 8: LB(2, 8, P_) break;
+                    default: LB(2, 16, P_)
+                }
+            };
+            switch (pq) {
+                case 1: go(std::integral_constant<int, 1>{}); break;
+                case 2: go(std::integral_constant<int, 2>{}); break;
+                case 3: go(std::integral_constant<int, 3>{}); break;
+                case 4: go(std::integral_constant<int, 4>{}); break;
+                case 5: go(std::integral_constant<int, 5>{}); break;
+                default: go(std::integral_constant<int, 0>{});
+            }
+        } else {
+            switch (nr) {
+                case 1: LB(2, 1, 0) break;
+                case 2: LB(2, 2, 0) break;
+                case 4: LB(2, 4, 0) break;
+                default: LB(2, 8, 0)
+            }
+        }
+#undef LB
+        CK(cudaGetLastError());
+        return;
+    }
+    BatchId<R> a{};
+    a.ninst = n;
+    size_t sm = 0;
+    int items = 0;
+    for (int k = 0; k < n; ++k) {
+        const E& e = ents[k];
+        const DevStage<R>& ds = stages_of<R>(dps[e.i])[e.sidx];
+        a.st[k] = type == BT_C1 ? ds.ids1 : ds.ids;
+        a.src[k] = e.src;
+        a.dst[k] = e.dst;
+        a.nrhs[k] = nrhs[e.i];
+        a.conj[k] = adjoint[e.i] != 0;
+        a.item0[k] = items;
+        if (type == BT_R) {
+            items += ds.n_items_r;
+            sm = std::max(sm, pattern_r_smem<R>(ds.max_nred, rt, nr));
+        } else if (type == BT_C1) {
+            items += ds.n_items_c1;
+            sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1));
+        } else {
+            items += ds.n_items_c;
+            sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, nr));
+        }
+    }
+    a.item0[n] = items;
+    if (items == 0) return;
+#define LK(KF)                                \
+    {                                         \
+        auto kf = KF;                         \
+        set_smem(kf, sm);                     \
+        kf<<<items, kThreads, sm, s>>>(a);    \
+    }
+    if (type == BT_C1) {
+        LK(k_batch_c1<R>)
+    } else if (type == BT_R) {
+        auto go = [&](auto rtc) {
+            constexpr int RT_ = decltype(rtc)::value;
+            switch (nr) {
+                case 1: LK((k_batch_r<R, RT_, 1>)) break;
+                case 2: LK((k_batch_r<R, RT_, 2>)) break;
+                case 4: LK((k_batch_r<R, RT_, 4>)) break;
+                case 8: LK((k_batch_r<R, RT_, 8>)) break;
+                default:
+                    if constexpr (sizeof(R) == 4) LK((k_batch_r<R, RT_, 16>))
+                    else LK((k_batch_r<R, RT_, 8>))
+            }
+        };
+        if (rt == 1) go(std::integral_constant<int, 1>{});
+        else go(std::integral_constant<int, 2>{});
+    } else {
+        switch (nr) {
+            case 1: LK((k_batch_c<R, 1>)) break;
+            case 2: LK((k_batch_c<R, 2>)) break;
+            case 4: LK((k_batch_c<R, 4>)) break;
+            case 8: LK((k_batch_c<R, 8>)) break;
+            default:
+                if constexpr (sizeof(R) == 4) LK((k_batch_c<R, 16>))
+                else LK((k_batch_c<R, 8>))
+        }
+    }
+#undef LK
+    CK(cudaGetLastError());
+}
+
+template <class R>
+void run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
+                 const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, cudaStream_t s,
+                 char* ws) {
+    std::vector<cx<R>*> b0(count), b1(count);
+    size_t off = 0;
+    int maxst = 0;
+    for (int i = 0; i < count; ++i) {
+        b0[i] = reinterpret_cast<cx<R>*>(ws + off);
+        b1[i] = b0[i] + dps[i]->max_space * nrhs[i];
+        off += instance_workspace(dps[i], nrhs[i]);
+        maxst = std::max(maxst, (int)stages_of<R>(dps[i]).size());
+    }
+    for (int q = 0; q < maxst; ++q) {
+        struct Entry { int i, sidx; VecRef<R> src, dst; };
+        std::map<std::array<int, 4>, std::vector<Entry>> groups;
+        for (int i = 0; i < count; ++i) {
+            const auto& sts = stages_of<R>(dps[i]);
+            const int ns = (int)sts.size();
+            if (q >= ns) continue;
+            const bool adj = adjoint[i] != 0;
+            const int sidx = adj ? ns - 1 - q : q;
+            const DevStage<R>& ds = sts[sidx];
+            const int nr = nrhs[i];
+            VecRef<R> uin{(cx<R>*)in[i], 1, ldin[i]}, uout{(cx<R>*)out[i], 1, ldout[i]};
+            auto internal = [&](int space) { return VecRef<R>{(space & 1) ? b1[i] : b0[i], nr, 1}; };
+            VecRef<R> fin = sidx == 0 ? (adj ? uout : uin) : internal(sidx - 1);
+            VecRef<R> fout = ds.out_user ? (adj ? uin : uout) : internal(sidx);
+            Entry e{i, sidx, adj ? fout : fin, adj ? fin : fout};
+            std::array<int, 4> key{};
+            if (ds.id) {
+                const bool wide_is_fwd_input = ds.kind != KIND_U;
+                const bool use_r = adj ? !wide_is_fwd_input : wide_is_fwd_input;
+                if (use_r) {
+                    const int t = pick_nr<R>(nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
+                    key = {BT_R, ds.rt, t, 0};
+                } else if (nr == 1 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
+                    key = {BT_C1, 0, 1, 0};
+                } else {
+                    const int t = pick_nr<R>(nr, [&](int qq) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, qq); });
+                    key = {BT_C, 0, t, 0};
+                }
+            } else {
+                const int t = pick_nr<R>(nr, [&](int qq) {
+                    return s_fly_smem<R>(ds.ss.P, ds.ss.Q, qq <= 4 && sizeof(R) == 4 ? 4 : 2, qq);
+                });
+                const int rt = (t <= 4 && sizeof(R) == 4) ? 4 : 2;
+                const int pq = sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0;
+                key = {BT_S, rt, t, pq};
+            }
+            groups[key].push_back(e);
+        }
+        for (auto& kv : groups) {
+            const auto& key = kv.first;
+            const auto& ents = kv.second;
+            for (size_t g0 = 0; g0 < ents.size(); g0 += kBatch) {
+                const int n = (int)std::min<size_t>(kBatch, ents.size() - g0);
+                launch_batch_group<R>(dps, key, &ents[g0], n, nrhs, adjoint, s);
+            }
+        }
     }
 }
 
@@ -717,6 +979,54 @@ int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
         else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::exception& e) {
+        set_last_error(e.what());
+        return MIDBF_EINTERNAL;
+    }
+}
+
+
+int midbf_batched_workspace_size(int count, const midbf_dplan* const* dps, const int* nrhs, size_t* bytes) {
+    if (count <= 0 || !dps || !nrhs || !bytes) {
+        set_last_error("midbf_batched_workspace_size: bad argument");
+        return MIDBF_EINVAL;
+    }
+    size_t b = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!dps[i] || nrhs[i] <= 0) {
+            set_last_error("midbf_batched_workspace_size: bad instance");
+            return MIDBF_EINVAL;
+        }
+        b += instance_workspace(dps[i], nrhs[i]);
+    }
+    *bytes = b;
+    return MIDBF_OK;
+}
+
+int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
+                        const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, void* stream,
+                        void* workspace, size_t workspace_bytes) {
+    try {
+        if (count <= 0 || !dps || !adjoint || !in || !ldin || !out || !ldout || !nrhs) fail(MIDBF_EINVAL, "null argument");
+        const int prec = dps[0] ? dps[0]->precision : -1;
+        for (int i = 0; i < count; ++i) {
+            const midbf_dplan* dp = dps[i];
+            if (!dp || !in[i] || !out[i] || nrhs[i] <= 0) fail(MIDBF_EINVAL, "bad instance " + std::to_string(i));
+            if (dp->precision != prec) fail(MIDBF_EINVAL, "all instances must share one precision");
+            if (dp->device != dps[0]->device) fail(MIDBF_EINVAL, "all instances must live on one device");
+            const int64_t nin = adjoint[i] ? dp->nx : dp->nw, nout = adjoint[i] ? dp->nw : dp->nx;
+            if (ldin[i] < nin || ldout[i] < nout) fail(MIDBF_EINVAL, "leading dimension too small for instance " + std::to_string(i));
+        }
+        size_t need = 0;
+        midbf_batched_workspace_size(count, dps, nrhs, &need);
+        if (!workspace || workspace_bytes < need) fail(MIDBF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (prec == MIDBF_FP32) run_batched<float>(count, dps, adjoint, in, ldin, out, ldout, nrhs, s, static_cast<char*>(workspace));
+        else run_batched<double>(count, dps, adjoint, in, ldin, out, ldout, nrhs, s, static_cast<char*>(workspace));
         return MIDBF_OK;
     } catch (const Error& e) {
         set_last_error(e.what());
