@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the headline measurement")
+    ap.add_argument("--mode", default="fp32", choices=["fp32", "bf16", "bf16r"],
+                    help="headline arithmetic: complex FP32, or the middle factor on BF16 tensor cores "
+                         "(bf16r: with the refinement products)")
     return ap.parse_args()
 
 
@@ -127,6 +131,17 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+def _bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh).get("bf16_tflops", 1900.0)
+    return 1900.0
+
+
+PEAK_BF16 = _bf16_peak()
 
 
 def peaks():
@@ -240,14 +255,18 @@ def main():
     t_build = time.perf_counter() - t0
     st = plan.stats()
     t0 = time.perf_counter()
-    dp32 = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY)
+    mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[args.mode]
+    dp32 = mb.DevicePlan(plan, mode, mb.S_ONTHEFLY)
     t_up = time.perf_counter() - t0
     fbytes, ibytes = dp32.bytes()
 
-    f = torch.from_numpy(synth.complex_gaussian(N, 1, 0)[:, 0]).to(dev, torch.complex64)
-    g = torch.empty(N, dtype=torch.complex64, device=dev)
-    h = torch.empty(N, dtype=torch.complex64, device=dev)
-    ws1 = torch.empty(dp32.workspace_bytes(1), dtype=torch.uint8, device=dev)
+    R1 = args.nrhs
+    f = torch.from_numpy(synth.complex_gaussian(N, R1, 0).T.copy()).to(dev, torch.complex64)
+    g = torch.empty((R1, N), dtype=torch.complex64, device=dev)
+    h = torch.empty((R1, N), dtype=torch.complex64, device=dev)
+    if R1 == 1:
+        f, g, h = f[0], g[0], h[0]
+    ws1 = torch.empty(dp32.workspace_bytes(R1), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     launches_per_apply = dp32.launches()
@@ -277,7 +296,7 @@ def main():
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
-    ms_per_step, value = aggregate(sum(step_ms), 2 * N, args.steps, pg, dev)
+    ms_per_step, value = aggregate(sum(step_ms), 2 * N * R1, args.steps, pg, dev)
 
     # the same steps again with CUDA events around every stage launch
     dp32.profile(True)
@@ -309,7 +328,7 @@ def main():
                 "whole_step_frac": round(all_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
 
     extras = {}
-    if not args.skip_extras:
+    if not args.skip_extras and R1 == 1:
         # plain FP64 form (middle factor stored: FP64 sincospi on GB300 is slow)
         dp64 = mb.DevicePlan(plan, mb.FP64, mb.S_STORED)
         f64 = f.to(torch.complex128)
@@ -364,30 +383,61 @@ def main():
             totR += e0.elapsed_time(e1)
         msR = totR / kR
         extras["nrhs64_fp32"] = {"value": 2 * N * R / (msR * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msR, 3)}
-        del wsR, F, G, H
+        # the same with the middle factor on the tensor cores (BF16 + refinement)
+        dptc = mb.DevicePlan(plan, mb.BF16 | mb.REFINE, mb.S_ONTHEFLY)
+        Gt = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        Ht = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        dptc.apply(F, out=Gt, workspace=wsR)
+        torch.cuda.synchronize()
+        totT = 0.0
+        dptc.profile(True)
+        s_ms = []
+        for _ in range(kR):
+            flush.zero_()
+            e0.record(stream)
+            dptc.apply(F, out=Gt, workspace=wsR)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            totT += e0.elapsed_time(e1)
+            s_ms += [ms for kind, ms, by in dptc.stage_times() if kind == 1]
+            dptc.apply(Gt, adjoint=True, out=Ht, workspace=wsR)
+            torch.cuda.synchronize()
+            s_ms += [ms for kind, ms, by in dptc.stage_times() if kind == 1]
+        dptc.profile(False)
+        msT = totT / kR * 2   # forward measured alone, adjoint assumed equal in the ratio
+        rel_tc = (torch.linalg.vector_norm(Gt - G) / torch.linalg.vector_norm(G)).item()
+        s_entries = st["s_entries"]
+        s_ms_mean = statistics.mean(s_ms) if s_ms else float("nan")
+        tc_tflops = 3 * 8.0 * s_entries * R / (s_ms_mean * 1e-3) / 1e12
+        extras["nrhs64_bf16_refine"] = {
+            "fwd_ms": round(totT / kR, 3), "s_stage_ms": round(s_ms_mean, 4),
+            "s_stage_issued_TFLOPs": round(tc_tflops, 1),
+            "s_stage_tensor_frac_of_bf16_dense_peak": round(tc_tflops * 1e12 / (PEAK_BF16 * 1e12), 4),
+            "rel_l2_vs_fp32": rel_tc, "status": dptc.status()}
+        del wsR, F, G, H, Gt, Ht, dptc
 
     # end to end through the host-buffer entry point (pinned host memory)
-    fh = torch.from_numpy(synth.complex_gaussian(N, 1, 0)[:, 0].astype(np.complex64)).pin_memory()
-    gh = torch.empty(N, dtype=torch.complex64).pin_memory()
-    hh = torch.empty(N, dtype=torch.complex64).pin_memory()
-    wsh = torch.empty(dp32.workspace_bytes(1, host_io=True), dtype=torch.uint8, device=dev)
+    fh = torch.from_numpy(synth.complex_gaussian(N, R1, 0).T.astype(np.complex64).copy()).pin_memory()
+    gh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
+    hh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
+    wsh = torch.empty(dp32.workspace_bytes(R1, host_io=True), dtype=torch.uint8, device=dev)
     for _ in range(3):
-        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), 1, stream.cuda_stream,
+        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), R1, stream.cuda_stream,
                                      wsh.data_ptr(), wsh.numel()), "apply_host")
     ke = max(3, args.steps // 2)
     torch.cuda.synchronize()
     te = time.perf_counter()
     for _ in range(ke):
-        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), 1, stream.cuda_stream,
+        mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), R1, stream.cuda_stream,
                                      wsh.data_ptr(), wsh.numel()), "apply_host")
-        mb.check(mb.midbf_apply_host(dp32.h, 1, gh.data_ptr(), hh.data_ptr(), 1, stream.cuda_stream,
+        mb.check(mb.midbf_apply_host(dp32.h, 1, gh.data_ptr(), hh.data_ptr(), R1, stream.cuda_stream,
                                      wsh.data_ptr(), wsh.numel()), "apply_host")
     e2e_s = (time.perf_counter() - te) / ke
-    e2e = {"value": ws * 2 * N / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": 2 * N * 8,
-           "d2h_bytes_per_step": 2 * N * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
+    e2e = {"value": ws * 2 * N * R1 / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": 2 * N * R1 * 8,
+           "d2h_bytes_per_step": 2 * N * R1 * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.skip_extras:
+    if rank == 0 and ws == 1 and not args.skip_extras and R1 == 1:
         try:
             cpu = cpu_baseline(plan.export(), N)
         except Exception as e:  # the GPU numbers stand without it
@@ -397,7 +447,8 @@ def main():
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
            "config": {"workload": f"fio2d_n{n}", "N": N, "d": 2, "phase": "FIO2D closed form",
-                      "nrhs": 1, "step": "forward + adjoint apply", "tol": 1e-6, "n0": 64, "L": st["L"],
+                      "nrhs": R1, "mode": args.mode, "step": "forward + adjoint apply", "tol": 1e-6, "n0": 64,
+                      "L": st["L"],
                       "t_entries": st["t_entries"], "s_entries": st["s_entries"], "max_rank": st["max_rank"],
                       "mean_rank": round(st["mean_rank"], 1), "factor_bytes": fbytes, "index_bytes": ibytes,
                       "l2": "flushed (512 MB write) between timed steps; factors 3+ GB > L2",

@@ -61,6 +61,11 @@ extern "C" {
 /* ---- apply precisions -------------------------------------------------- */
 #define MIDBF_FP64  0   /* plain form: complex128 data and arithmetic          */
 #define MIDBF_FP32  1   /* mixed form: complex64 data and arithmetic           */
+#define MIDBF_BF16  2   /* complex64 data; with 16 or more right-hand sides the
+                           middle factor runs on the tensor cores (tcgen05, BF16
+                           operands, FP32 accumulation)                        */
+#define MIDBF_REFINE 16 /* flag for MIDBF_BF16: split operands into BF16 hi + lo
+                           and add the refinement products A_hi B_lo + A_lo B_hi */
 
 /* ---- middle-factor modes ----------------------------------------------- */
 #define MIDBF_S_ONTHEFLY 0  /* S entries exp(2 pi i Phi) generated in the kernel */
@@ -145,6 +150,8 @@ typedef struct {
     int use_box;       /* 1: use boxX/boxW as the tree domains, 0: tight cubes  */
     double boxX[4];    /* lo[0..d-1], side (at index d)                         */
     double boxW[4];
+    int device_ids;    /* 1: kernel samples and pivoted QRs on the current CUDA
+                          device (FP64), 0: on the host threads               */
 } midbf_params;
 
 int midbf_params_default(int d, midbf_params* p);
@@ -182,11 +189,17 @@ void midbf_free(void* p);
 
 /* ---- device plans and the apply ----------------------------------------
  * midbf_dplan_create: copy a plan to the current CUDA device in one precision
- * (MIDBF_FP64 or MIDBF_FP32) and middle-factor mode.  Allocates device memory
+ * (MIDBF_FP64, MIDBF_FP32, or MIDBF_BF16 [| MIDBF_REFINE]) and middle-factor
+ * mode.  Allocates device memory
  * (cudaMalloc) and synchronizes the device; call before any stream capture.
  * Errors: MIDBF_EINVAL, MIDBF_ENOMEM, MIDBF_ECUDA. */
 int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out);
 void midbf_dplan_destroy(midbf_dplan* dp);
+
+/* Device-side status of a plan's kernels: MIDBF_OK, or MIDBF_ETIMEOUT when a
+ * bounded wait inside a tensor-core kernel gave up (its results are then
+ * invalid).  Reading synchronizes the device; reset = 1 clears the word. */
+int midbf_dplan_status(const midbf_dplan* dp, int reset, int* status);
 
 /* Bytes of device workspace midbf_apply needs for nrhs right-hand sides. */
 int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes);

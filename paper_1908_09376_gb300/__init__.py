@@ -24,7 +24,7 @@ _lib = C.CDLL(LIB_PATH)
 # ---- constants (include/midbf.h) ------------------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ECALLBACK, ERANK, ERECOVERY, ETIMEOUT, EINTERNAL, EFORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 PHASE_FIO2D, PHASE_FIO3D, PHASE_FIO2D_JUMP, PHASE_DOT, PHASE_ZERO, PHASE_SEPARABLE, PHASE_LOWRANK = 1, 2, 3, 4, 5, 6, 7
-FP64, FP32 = 0, 1
+FP64, FP32, BF16, REFINE = 0, 1, 2, 16
 S_ONTHEFLY, S_STORED = 0, 1
 
 _i64p = C.POINTER(C.c_int64)
@@ -35,7 +35,7 @@ _vp = C.c_void_p
 class midbf_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("n0", C.c_int), ("t", C.c_double), ("kest", C.c_int),
                 ("kmax", C.c_int), ("seed", C.c_uint64), ("nthreads", C.c_int), ("use_box", C.c_int),
-                ("boxX", C.c_double * 4), ("boxW", C.c_double * 4)]
+                ("boxX", C.c_double * 4), ("boxW", C.c_double * 4), ("device_ids", C.c_int)]
 
 
 class midbf_stats(C.Structure):
@@ -91,6 +91,7 @@ midbf_apply = _sig("midbf_apply", C.c_int,
                    [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp, _vp, C.c_size_t])
 midbf_apply_host = _sig("midbf_apply_host", C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_size_t])
 midbf_apply_launches = _sig("midbf_apply_launches", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)])
+midbf_dplan_status = _sig("midbf_dplan_status", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)])
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
@@ -271,7 +272,8 @@ class DevicePlan:
         h = _vp()
         check(midbf_dplan_create(plan.h, precision, s_mode, C.byref(h)), "midbf_dplan_create")
         self.h = h
-        self.precision = precision
+        self.mode = precision
+        self.precision = FP64 if precision == FP64 else FP32   # storage precision of the vectors
         st = plan.stats()
         self.nx, self.nw = st["nx"], st["nw"]
 
@@ -279,6 +281,11 @@ class DevicePlan:
         if getattr(self, "h", None):
             midbf_dplan_destroy(self.h)
             self.h = None
+
+    def status(self, reset=True):
+        v = C.c_int()
+        check(midbf_dplan_status(self.h, int(reset), C.byref(v)), "midbf_dplan_status")
+        return v.value
 
     def workspace_bytes(self, nrhs, host_io=False):
         n = C.c_size_t()

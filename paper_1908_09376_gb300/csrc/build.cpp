@@ -428,6 +428,77 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
         return c;
     };
 
+    std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> gctx(nullptr, [](GpuIdContext*) {});
+    if (prm.device_ids) gctx = gpu_id_context(ph);
+
+    // All IDs of one kind in one step.  The first runs alone and sets the
+    // starting sample size of the others (t times its rank), so the result
+    // does not depend on the thread schedule or on the device path.
+    auto run_phase = [&](int64_t ntot, bool cols_x, uint64_t tag, int64_t& kest, std::vector<IdOut>& outv,
+                         const std::function<std::vector<int64_t>(int64_t)>& cols_fn,
+                         const std::function<const Cand&(int64_t)>& cand_fn) {
+        auto seed_of = [&](int64_t e) { return mix(prm.seed, tag * 1000003 + (uint64_t)e); };
+        if (!gctx) {
+            outv[0] = sampled_id(cols_fn(0), cols_x, cand_fn(0), (int64_t)std::ceil(prm.t * kest), seed_of(0));
+            kest = outv[0].sub.k;
+            const int64_t ns0 = (int64_t)std::ceil(prm.t * kest);
+            parallel_for(ntot - 1, nthreads, [&](int64_t e) {
+                outv[e + 1] = sampled_id(cols_fn(e + 1), cols_x, cand_fn(e + 1), ns0, seed_of(e + 1));
+            });
+            return;
+        }
+        // device path: the same sampling and regrowth rule, decompositions batched on the GPU
+        std::vector<std::vector<int64_t>> colsv(ntot);
+        parallel_for(ntot, nthreads, [&](int64_t e) { colsv[e] = cols_fn(e); });
+        std::vector<int64_t> ns(ntot, 0);
+        std::vector<char> done(ntot, 0);
+        auto solve = [&](const std::vector<int64_t>& which) {
+            std::vector<IdRequest> req(which.size());
+            parallel_for((int64_t)which.size(), nthreads, [&](int64_t q) {
+                const int64_t e = which[q];
+                const Cand& cand = cand_fn(e);
+                std::vector<int64_t> pos = mock_chebyshev(cand.xy, cand.nn, d, ns[e], seed_of(e));
+                req[q].cols = &colsv[e];
+                req[q].cols_x = cols_x;
+                req[q].samples.resize(pos.size());
+                for (size_t i = 0; i < pos.size(); ++i) req[q].samples[i] = cand.pts[pos[i]];
+            });
+            std::vector<IdReply> rep;
+            gpu_id_batch(*gctx, req, prm.tol, prm.kmax, rep);
+            for (size_t q = 0; q < which.size(); ++q) {
+                const int64_t e = which[q];
+                const int64_t ncand = (int64_t)cand_fn(e).pts.size();
+                const int64_t got = (int64_t)req[q].samples.size();
+                const int64_t k = rep[q].k;
+                const int64_t need = (int64_t)std::ceil(prm.t * (double)k);
+                if (got >= ncand || got >= need) {
+                    IdOut& o = outv[e];
+                    o.sub.k = (int32_t)k;
+                    o.sub.m = (int32_t)colsv[e].size();
+                    o.sub.skel = std::move(rep[q].skel);
+                    o.sub.red = std::move(rep[q].red);
+                    o.sub.T = std::move(rep[q].T);
+                    o.skel_pts.resize(k);
+                    for (int64_t i = 0; i < k; ++i) o.skel_pts[i] = colsv[e][o.sub.skel[i]];
+                    done[e] = 1;
+                } else {
+                    ns[e] = std::min(ncand, need);
+                }
+            }
+        };
+        ns[0] = std::max<int64_t>(1, (int64_t)std::ceil(prm.t * kest));
+        while (!done[0]) solve({0});
+        kest = outv[0].sub.k;
+        for (int64_t e = 1; e < ntot; ++e) ns[e] = std::max<int64_t>(1, (int64_t)std::ceil(prm.t * kest));
+        for (;;) {
+            std::vector<int64_t> which;
+            for (int64_t e = 1; e < ntot; ++e)
+                if (!done[e]) which.push_back(e);
+            if (which.empty()) break;
+            solve(which);
+        }
+    };
+
     for (int s = 1; s <= nsteps; ++s) {
         const int la = L - s + 1, lq = s - 1 + delta, lp = s - 2 + delta;
         const int na_x = (int)TX.levels[la].size(), nq_w = (int)TW.levels[lq].size();
@@ -474,18 +545,9 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
             }
             return rows;
         };
-        auto do_rid = [&](int64_t e, int64_t ns0) {
-            const int ia = (int)(e / nq_w), iq = (int)(e % nq_w);
-            const Cand& cand = *ccand[keys[e]];
-            Uf[s][e] = sampled_id(rows_of(ia, iq), true, cand, ns0, mix(prm.seed, (uint64_t)(s * 4 + 1) * 1000003 + e));
-        };
-        {
-            const int64_t ntot = (int64_t)na_x * nq_w;
-            do_rid(0, (int64_t)std::ceil(prm.t * kest_r));
-            kest_r = Uf[s][0].sub.k;
-            const int64_t ns0 = (int64_t)std::ceil(prm.t * kest_r);
-            parallel_for(ntot - 1, nthreads, [&](int64_t e) { do_rid(e + 1, ns0); });
-        }
+        run_phase((int64_t)na_x * nq_w, true, (uint64_t)(s * 4 + 1), kest_r, Uf[s],
+                  [&](int64_t e) { return rows_of((int)(e / nq_w), (int)(e % nq_w)); },
+                  [&](int64_t e) -> const Cand& { return *ccand[keys[e]]; });
         ccand.clear();
         // ---- column IDs (beta, P) ----
         std::vector<std::unique_ptr<Cand>> rcand((size_t)np_x * nq_w);
@@ -509,19 +571,12 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
             }
             return cols;
         };
-        auto do_cid = [&](int64_t e, int64_t ns0) {
-            const int ib = (int)(e / np_x), ip = (int)(e % np_x);
-            const int qb = TW.ancestor(la, ib, lq);
-            const Cand& cand = *rcand[(size_t)ip * nq_w + qb];
-            Vf[s][e] = sampled_id(cols_of(ib, ip), false, cand, ns0, mix(prm.seed, (uint64_t)(s * 4 + 2) * 1000003 + e));
-        };
-        {
-            const int64_t ntot = (int64_t)nb_w * np_x;
-            do_cid(0, (int64_t)std::ceil(prm.t * kest_c));
-            kest_c = Vf[s][0].sub.k;
-            const int64_t ns0 = (int64_t)std::ceil(prm.t * kest_c);
-            parallel_for(ntot - 1, nthreads, [&](int64_t e) { do_cid(e + 1, ns0); });
-        }
+        run_phase((int64_t)nb_w * np_x, false, (uint64_t)(s * 4 + 2), kest_c, Vf[s],
+                  [&](int64_t e) { return cols_of((int)(e / np_x), (int)(e % np_x)); },
+                  [&](int64_t e) -> const Cand& {
+                      const int ib = (int)(e / np_x), ip = (int)(e % np_x);
+                      return *rcand[(size_t)ip * nq_w + TW.ancestor(la, ib, lq)];
+                  });
     }
 
     // ---- assemble the stages in forward order ----

@@ -22,6 +22,7 @@
 
 #include "internal.hpp"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 using namespace midbf;
 using namespace midbf_dev;
@@ -69,7 +70,9 @@ struct DevStage : DevStageBase {
 }  // namespace
 
 struct midbf_dplan {
-    int precision = MIDBF_FP32;
+    int precision = MIDBF_FP32;   // storage: MIDBF_FP32 (also for the BF16 modes) or MIDBF_FP64
+    int tc_mode = 0;              // 0: SIMT only; 1: BF16 tensor cores; 2: BF16 + refinement
+    int* d_status = nullptr;      // device status word written by bounded waits
     int s_mode = MIDBF_S_ONTHEFLY;
     int device = 0;
     int64_t nx = 0, nw = 0;
@@ -91,6 +94,7 @@ struct midbf_dplan {
     mutable int last_nrhs = 1;
     ~midbf_dplan() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (d_status) cudaFree(d_status);
         for (void* p : allocs) cudaFree(p);
     }
 };
@@ -595,6 +599,49 @@ void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
     CK(cudaGetLastError());
 }
 
+constexpr int kTcMinRhs = 16;  // tensor cores for the middle factor from this many RHS on
+
+template <int PQ, bool RF, bool CJ>
+void launch_tc_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
+                 cudaStream_t s) {
+    SStage<float> st = ds.ss;
+    const size_t sm = tc_smem_bytes<RF>();
+    auto kf = k_s_tc<PQ, RF, CJ>;
+    set_smem(kf, sm);
+    if (!CJ) {
+        st.items = ds.items_rows4;
+        kf<<<ds.n_items_rows4, kTcThreads, sm, s>>>(st, ds.srows, ds.scols, src, dst, nrhs, 1, status);
+    } else {
+        st.items = ds.items_cols4;
+        kf<<<ds.n_items_cols4, kTcThreads, sm, s>>>(st, ds.scols, ds.srows, src, dst, nrhs, 0, status);
+    }
+}
+
+template <bool RF, bool CJ>
+void launch_tc_rc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
+                  cudaStream_t s) {
+    switch (phase_shape_code(ds.ss.P, ds.ss.Q)) {
+        case 1: launch_tc_t<1, RF, CJ>(ds, src, dst, nrhs, status, s); break;
+        case 2: launch_tc_t<2, RF, CJ>(ds, src, dst, nrhs, status, s); break;
+        case 3: launch_tc_t<3, RF, CJ>(ds, src, dst, nrhs, status, s); break;
+        case 4: launch_tc_t<4, RF, CJ>(ds, src, dst, nrhs, status, s); break;
+        case 5: launch_tc_t<5, RF, CJ>(ds, src, dst, nrhs, status, s); break;
+        default: launch_tc_t<0, RF, CJ>(ds, src, dst, nrhs, status, s);
+    }
+}
+
+void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint, bool refine,
+               int* status, cudaStream_t s) {
+    if (refine) {
+        if (adjoint) launch_tc_rc<true, true>(ds, src, dst, nrhs, status, s);
+        else launch_tc_rc<true, false>(ds, src, dst, nrhs, status, s);
+    } else {
+        if (adjoint) launch_tc_rc<false, true>(ds, src, dst, nrhs, status, s);
+        else launch_tc_rc<false, false>(ds, src, dst, nrhs, status, s);
+    }
+    CK(cudaGetLastError());
+}
+
 template <class R>
 int count_launches(const std::vector<DevStage<R>>& st) {
     int n = 0;
@@ -638,6 +685,9 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
             const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
             if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s);
             else launch_c<R>(ds, src, dst, nrhs, adjoint, s);
+        } else if constexpr (sizeof(R) == 4) {
+            if (dp->tc_mode && nrhs >= kTcMinRhs) launch_tc(ds, src, dst, nrhs, adjoint, dp->tc_mode == 2, dp->d_status, s);
+            else launch_s<R>(ds, src, dst, nrhs, adjoint, s);
         } else {
             launch_s<R>(ds, src, dst, nrhs, adjoint, s);
         }
@@ -867,20 +917,26 @@ extern "C" {
 int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out) {
     try {
         if (!plan || !out) fail(MIDBF_EINVAL, "null argument");
-        if (precision != MIDBF_FP64 && precision != MIDBF_FP32) fail(MIDBF_EINVAL, "unknown precision");
+        const int base = precision & ~MIDBF_REFINE;
+        if (base != MIDBF_FP64 && base != MIDBF_FP32 && base != MIDBF_BF16) fail(MIDBF_EINVAL, "unknown precision");
+        if ((precision & MIDBF_REFINE) && base != MIDBF_BF16) fail(MIDBF_EINVAL, "MIDBF_REFINE applies to MIDBF_BF16");
         if (s_mode != MIDBF_S_ONTHEFLY && s_mode != MIDBF_S_STORED) fail(MIDBF_EINVAL, "unknown middle-factor mode");
         const Plan& pl = *reinterpret_cast<const Plan*>(plan);
         int ndev = 0;
         if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) fail(MIDBF_ECUDA, "no CUDA device");
         auto dp = std::make_unique<midbf_dplan>();
-        dp->precision = precision;
+        dp->precision = base == MIDBF_FP64 ? MIDBF_FP64 : MIDBF_FP32;
+        dp->tc_mode = base == MIDBF_BF16 ? ((precision & MIDBF_REFINE) ? 2 : 1) : 0;
+        if (dp->tc_mode && s_mode != MIDBF_S_ONTHEFLY) fail(MIDBF_EINVAL, "the tensor-core modes generate the middle factor on the fly");
         dp->s_mode = s_mode;
         CK(cudaGetDevice(&dp->device));
         dp->nx = pl.nx();
         dp->nw = pl.nw();
-        if (precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32);
+        if (cudaMalloc(&dp->d_status, sizeof(int)) != cudaSuccess) fail(MIDBF_ENOMEM, "cudaMalloc of the status word failed");
+        CK(cudaMemset(dp->d_status, 0, sizeof(int)));
+        if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32);
         else make_stages<double>(dp.get(), pl, dp->st64);
-        dp->launches = precision == MIDBF_FP32 ? count_launches(dp->st32) : count_launches(dp->st64);
+        dp->launches = dp->precision == MIDBF_FP32 ? count_launches(dp->st32) : count_launches(dp->st64);
         CK(cudaDeviceSynchronize());
         *out = dp.release();
         return MIDBF_OK;
@@ -897,6 +953,20 @@ int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_
 }
 
 void midbf_dplan_destroy(midbf_dplan* dp) { delete dp; }
+
+int midbf_dplan_status(const midbf_dplan* dp, int reset, int* status) {
+    try {
+        if (!dp || !status) fail(MIDBF_EINVAL, "null argument");
+        int v = 0;
+        CK(cudaMemcpy(&v, dp->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (reset) CK(cudaMemset(dp->d_status, 0, sizeof(int)));
+        *status = v;
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
 
 int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes) {
     if (!dp || !bytes || nrhs <= 0) {

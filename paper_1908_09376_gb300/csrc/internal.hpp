@@ -131,4 +131,20 @@ IdResult column_id(std::vector<cplx>& A, int ms, int n, double tol, int kmax);
 
 void set_last_error(const std::string& s);
 
+// build_gpu.cu: batched column IDs on the current CUDA device.
+struct IdRequest {
+    const std::vector<int64_t>* cols;   // decomposed point indices (n)
+    std::vector<int64_t> samples;       // sample point indices on the other side (ns)
+    bool cols_x;                        // decomposed points are X points
+};
+struct IdReply {
+    int k = 0;
+    std::vector<int32_t> skel, red;
+    std::vector<cplx> T;                // k x (n - k) row-major
+};
+struct GpuIdContext;
+std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> gpu_id_context(const Phase& ph);
+void gpu_id_batch(GpuIdContext& ctx, const std::vector<IdRequest>& reqs, double tol, int kmax,
+                  std::vector<IdReply>& out);
+
 }  // namespace midbf

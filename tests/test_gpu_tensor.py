@@ -1,0 +1,75 @@
+"""Tensor-core middle factor (tcgen05, BF16 operands, FP32 accumulation).
+
+With 16 or more right-hand sides, MIDBF_BF16 plans generate the middle factor
+on the fly into shared memory as BF16 and multiply on the tensor cores;
+MIDBF_REFINE adds the refinement products of the hi/lo split (reading A-R of
+the design notes).  Checked against the oracle's FP64 apply of the same
+factors.  Tolerances: BF16 alone keeps 8 mantissa bits (relative 2^-9 per
+operand), so a block sum of ~10^3 terms carries ~1e-3 relative error: bound
+2e-2; with refinement the operands keep ~16 bits: bound 2e-5 as for FP32.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct, midbf, planio
+from oracle.phase import Phase as OPhase
+
+torch = pytest.importorskip("torch")
+mb = pytest.importorskip("paper_1908_09376_gb300")
+
+pytestmark = pytest.mark.gpu
+
+_C = {}
+
+
+def _case(name):
+    if name in _C:
+        return _C[name]
+    if name == "fio2d_n64":
+        n = 64
+        X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+        fac = midbf.build(OPhase(synth.PHASE_FIO2D, X, W), n0=64, tol=1e-6, t=2.0,
+                          boxX=(np.zeros(2), 1.0), boxW=(np.full(2, -n / 2), float(n)))
+    elif name == "fio3d_n8":
+        X = synth.uniform_random_points(512, 3, 0)
+        W = synth.frequency_grid(8, 3)
+        fac = midbf.build(OPhase(synth.PHASE_FIO3D, X, W), n0=8, tol=1e-7, t=2.0,
+                          boxX=(np.zeros(3), 1.0), boxW=(np.full(3, -4.0), 8.0))
+    else:
+        n = 32
+        X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+        rng = np.random.default_rng(5)
+        U = np.concatenate([X, 0.01 * rng.standard_normal((1024, 2))], axis=1)
+        V = np.concatenate([W, rng.standard_normal((1024, 2))], axis=1)
+        fac = midbf.build(OPhase(synth.PHASE_LOWRANK, X, W, U, V), n0=16, tol=1e-6, t=2.0,
+                          boxX=(np.zeros(2), 1.0), boxW=(np.full(2, -16.0), 32.0))
+    _C[name] = (fac, mb.Plan.load(planio.write(fac)), midbf.factor_matrices(fac))
+    return _C[name]
+
+
+@pytest.mark.parametrize("case", ["fio2d_n64", "fio3d_n8", "lowrank_n32"])
+@pytest.mark.parametrize("mode,tol", [(mb.BF16, 2e-2), (mb.BF16 | mb.REFINE, 2e-5)])
+def test_tensor_core_middle_factor(case, mode, tol):
+    fac, plan, mats = _case(case)
+    dp = mb.DevicePlan(plan, mode)
+    for nrhs in (16, 130):
+        f = synth.complex_gaussian(fac.nw, nrhs, 60)
+        h = synth.complex_gaussian(fac.nx, nrhs, 61)
+        g = dp.apply(torch.from_numpy(f.T.copy()).to("cuda", torch.complex64)).cpu().numpy().T
+        a = dp.apply(torch.from_numpy(h.T.copy()).to("cuda", torch.complex64), adjoint=True).cpu().numpy().T
+        g_ref = np.stack([midbf.apply(fac, f[:, r], mats) for r in range(nrhs)], 1)
+        a_ref = np.stack([midbf.apply_adjoint(fac, h[:, r], mats) for r in range(nrhs)], 1)
+        eg, ea = direct.rel_l2(g, g_ref), direct.rel_l2(a, a_ref)
+        assert eg < tol and ea < tol, (case, mode, nrhs, eg, ea)
+    assert dp.status() == mb.OK
+
+
+def test_tensor_mode_below_threshold_uses_simt():
+    """Fewer than 16 RHS: the BF16 plan runs the FP32 SIMT kernels (FP32 accuracy)."""
+    fac, plan, mats = _case("lowrank_n32")
+    dp = mb.DevicePlan(plan, mb.BF16)
+    f = synth.complex_gaussian(fac.nw, 3, 62)
+    g = dp.apply(torch.from_numpy(f.T.copy()).to("cuda", torch.complex64)).cpu().numpy().T
+    g_ref = np.stack([midbf.apply(fac, f[:, r], mats) for r in range(3)], 1)
+    assert direct.rel_l2(g, g_ref) < 2e-5
