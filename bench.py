@@ -1,17 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the MIDBF apply on GB300 (one JSON line on stdout).
 
-Workload: the 2D generalized Radon transform of Example 1 (Sec. 4) on the
-n = 256 grid, N = 65,536 points, phase x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
-ID tolerance 1e-6, n0 = 64 (L = 5).  Synthetic inputs (synth.py), seeded.
+Default workload: the 2D generalized Radon transform of Example 1 (Sec. 4)
+on the n = 256 grid, N = 65,536 points, phase x.xi + sqrt(c1^2 xi1^2 +
+c2^2 xi2^2), ID tolerance 1e-6, n0 = 64 (L = 5).  --workload selects the 3D
+variant (N = 32,768 random points, 256 RHS, BF16 tensor cores with the
+refinement products) or the 2D phase with a jump across x1 = 1/2 on the
+n = 1024 grid (16 RHS).  Synthetic inputs (synth.py), seeded.
 
 A step is one pass of the whole hot path over one batch: the forward apply
 g = K f followed by the adjoint apply K^H g, both through all levels (V
 levels, the on-the-fly middle factor, U levels), in the mixed form (complex
-FP32), 1 right-hand side.  value = points*RHS processed per second over all
-ranks (2 N per step per rank).  Extra keys report the plain FP64 form, 64
-right-hand sides, the roofline of the dominant kernel, the end-to-end time
-through the host-buffer C entry point, and the CPU oracle.
+FP32, or BF16 tensor cores with FP32 accumulation).  value = points*RHS
+processed per second over all ranks (2 N R per step per rank).  Extra keys
+report the rel-L2 error of the step's outputs against FP64 direct sums on
+sampled rows, the plain FP64 form, 64 right-hand sides, the roofline of the
+dominant kernel, the end-to-end time through the host-buffer C entry point,
+and the CPU oracle.
 
 Multi-GPU: the apply does not shard across GPUs here (replicas only); with
 torchrun each rank runs its own replica and value sums over ranks.
@@ -47,10 +52,15 @@ def parse():
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
-    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of the headline measurement")
-    ap.add_argument("--mode", default="fp32", choices=["fp32", "bf16", "bf16r"],
-                    help="headline arithmetic: complex FP32, or the middle factor on BF16 tensor cores "
-                         "(bf16r: with the refinement products)")
+    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump_n1024"],
+                    help="fio2d: 2D FIO phase on the n x n grid (--n); fio3d_n32: 3D, N = 32,768, random X; "
+                         "fio2d_jump_n1024: 2D with the jump |xi| sign(x1 - 1/2), N = 1,048,576")
+    ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's)")
+    ap.add_argument("--mode", default=None, choices=["fp32", "bf16", "bf16r"],
+                    help="arithmetic: complex FP32, or BF16 tensor cores with FP32 accumulation "
+                         "(bf16r: with the refinement products); default fp32, bf16r for fio3d_n32")
+    ap.add_argument("--build", default=None, choices=["host", "device"],
+                    help="where the interpolative decompositions run (default: host for fio2d, else device)")
     return ap.parse_args()
 
 
@@ -83,6 +93,56 @@ def workload(n):
     boxX = (np.zeros(2), 1.0)
     boxW = (np.full(2, -n / 2), float(n))
     return X, W, boxX, boxW
+
+
+def pick_workload(args):
+    """The synthetic workload, its RHS count, arithmetic and build site."""
+    if args.workload == "fio2d":
+        w = synth.Workload(f"fio2d_n{args.n}", 2, args.n, synth.PHASE_FIO2D, 1e-6, 64, 1, 0,
+                           sample_rows=256, sample_seed=3)
+    else:
+        w = synth.WORKLOADS[args.workload]
+    nrhs = args.nrhs if args.nrhs is not None else w.nrhs
+    mode = args.mode if args.mode is not None else ("bf16r" if w.d == 3 else "fp32")
+    build = args.build if args.build is not None else ("host" if args.workload == "fio2d" else "device")
+    return w, nrhs, mode, build
+
+
+PHASE_NAMES = {synth.PHASE_FIO2D: "FIO2D closed form", synth.PHASE_FIO3D: "FIO3D closed form",
+               synth.PHASE_FIO2D_JUMP: "FIO2D + jump closed form"}
+
+
+def sampled_direct_error(ph, F, G, H, rows, cols, chunk=16):
+    """rel-L2 of sampled outputs against FP64 direct sums (eq. (1)).
+
+    G = K F and H = K^H G as computed on the GPU ((R, N) arrays); for the
+    sampled rows i, sum_j exp(2 pi i Phi(x_i, xi_j)) F_j over every column j,
+    and for the sampled columns c, sum_i conj(exp(2 pi i Phi(x_i, xi_c))) G_i
+    over every row, with Phi from the library's FP64 phase evaluation (no part
+    of the apply path)."""
+    nx, nw = ph.nx, ph.nw
+    Fd = F.T.astype(np.complex128)
+    Gd = G.T.astype(np.complex128)
+    num = den = 0.0
+    for r0 in range(0, len(rows), chunk):
+        rr = rows[r0:r0 + chunk]
+        ix = np.repeat(rr, nw)
+        iw = np.tile(np.arange(nw, dtype=np.int64), len(rr))
+        K = np.exp(2j * np.pi * ph.eval(ix, iw)).reshape(len(rr), nw)
+        ref = K @ Fd
+        num += np.sum(np.abs(G[:, rr].T - ref) ** 2)
+        den += np.sum(np.abs(ref) ** 2)
+    e_fwd = math.sqrt(num / den)
+    num = den = 0.0
+    for c0 in range(0, len(cols), chunk):
+        cc = cols[c0:c0 + chunk]
+        ix = np.tile(np.arange(nx, dtype=np.int64), len(cc))
+        iw = np.repeat(cc, nx)
+        K = np.exp(-2j * np.pi * ph.eval(ix, iw)).reshape(len(cc), nx)
+        ref = K @ Gd
+        num += np.sum(np.abs(H[:, cc].T - ref) ** 2)
+        den += np.sum(np.abs(ref) ** 2)
+    return e_fwd, math.sqrt(num / den)
 
 
 class ClockSampler:
@@ -142,6 +202,7 @@ def _bf16_peak():
 
 
 PEAK_BF16 = _bf16_peak()
+PEAK_BF16_SOURCE = "measured (burst)" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"
 
 
 def peaks():
@@ -245,23 +306,26 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    n = args.n
-    N = n * n
-    X, W, bx, bw = workload(n)
+    wl, R1, mode_name, build_site = pick_workload(args)
+    n = wl.n
+    N = wl.N
+    X, W, bx, bw = wl.points()
 
     t0 = time.perf_counter()
-    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
-    plan = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, nthreads=args.threads)
+    ph = mb.Phase.closed_form(wl.phase, X, W)
+    plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads,
+                         device_ids=1 if build_site == "device" else 0)
     t_build = time.perf_counter() - t0
     st = plan.stats()
     t0 = time.perf_counter()
-    mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[args.mode]
+    mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[mode_name]
     dp32 = mb.DevicePlan(plan, mode, mb.S_ONTHEFLY)
     t_up = time.perf_counter() - t0
     fbytes, ibytes = dp32.bytes()
+    sinfo = dp32.stage_info()
 
-    R1 = args.nrhs
-    f = torch.from_numpy(synth.complex_gaussian(N, R1, 0).T.copy()).to(dev, torch.complex64)
+    f_host = synth.complex_gaussian(N, R1, wl.f_seed)
+    f = torch.from_numpy(f_host.T.copy()).to(dev, torch.complex64)
     g = torch.empty((R1, N), dtype=torch.complex64, device=dev)
     h = torch.empty((R1, N), dtype=torch.complex64, device=dev)
     if R1 == 1:
@@ -311,24 +375,59 @@ def main():
             stage_ms.setdefault(("adj", q, kind, by), []).append(ms)
     dp32.profile(False)
 
-    # dominant kernel and its roofline (algorithmic bytes / event-timed duration)
+    # dominant kernel and its roofline (algorithmic bytes or flops / event-timed duration)
     peak, peak_kind = peaks()
+    ns = len(sinfo)
+    tc_active = mode_name != "fp32" and R1 >= 16
+
+    def stage_flops(direction, q):
+        """Algorithmic flops of a stage launch: 8 per complex multiply-add of
+        the method's factor entries (T of the IDs, or the middle factor) per RHS."""
+        sidx = q if direction == "fwd" else ns - 1 - q
+        return 8.0 * sinfo[sidx][1] * R1
+
     dom = max(stage_ms.items(), key=lambda kv: statistics.mean(kv[1]))
     (direction, q, kind, by), times = dom
     dom_ms = statistics.mean(times)
-    achieved = by / (dom_ms * 1e-3) / 1e9
     all_bytes = sum(k[3] for k in stage_ms.keys())
-    stage_rows = [{"dir": k[0], "stage": k[1], "kind": "VSU"[k[2]], "ms": round(statistics.mean(v), 4),
-                   "GB": round(k[3] / 1e9, 4), "GBps": round(k[3] / (statistics.mean(v) * 1e-3) / 1e9, 1)}
-                  for k, v in sorted(stage_ms.items(), key=lambda kv: (kv[0][0] != "fwd", kv[0][1]))]
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": f"{direction} stage {q} ({'VSU'[kind]})", "peak_source": peak_kind,
-                "whole_step_GBps": round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1),
-                "whole_step_frac": round(all_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+    stage_rows = []
+    for k, v in sorted(stage_ms.items(), key=lambda kv: (kv[0][0] != "fwd", kv[0][1])):
+        ms_ = statistics.mean(v)
+        row = {"dir": k[0], "stage": k[1], "kind": "VSU"[k[2]], "ms": round(ms_, 4),
+               "GB": round(k[3] / 1e9, 4), "GBps": round(k[3] / (ms_ * 1e-3) / 1e9, 1)}
+        if tc_active:
+            row["TFLOPs"] = round(stage_flops(k[0], k[1]) / (ms_ * 1e-3) / 1e12, 1)
+        stage_rows.append(row)
+    if tc_active:
+        achieved = stage_flops(direction, q) / (dom_ms * 1e-3) / 1e12
+        issued = achieved * (3 if mode_name == "bf16r" else 1)
+        roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": PEAK_BF16, "unit": "TFLOP/s",
+                    "frac": round(achieved / PEAK_BF16, 4), "traffic": None,
+                    "kernel": f"{direction} stage {q} ({'VSU'[kind]})", "peak_source": PEAK_BF16_SOURCE,
+                    "issued_TFLOPs": round(issued, 1), "issued_frac": round(issued / PEAK_BF16, 4),
+                    "flops": "8 per complex multiply-add of the factor entries per RHS; refinement issues 3x"}
+    else:
+        achieved = by / (dom_ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": None,
+                    "kernel": f"{direction} stage {q} ({'VSU'[kind]})", "peak_source": peak_kind,
+                    "whole_step_GBps": round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1),
+                    "whole_step_frac": round(all_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
+
+    # accuracy of this run's outputs against FP64 direct sums on sampled rows / columns
+    acc = None
+    if rank == 0 and wl.sample_rows:
+        torch.cuda.synchronize()
+        Gn = g.reshape(R1, N).cpu().numpy()
+        Hn = h.reshape(R1, N).cpu().numpy()
+        rows = synth.sample_rows(N, wl.sample_rows, wl.sample_seed)
+        cols = synth.sample_rows(N, wl.sample_rows, wl.sample_seed + 1)
+        e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Hn, rows, cols)
+        acc = {"forward": e_f, "adjoint": e_a, "rows": int(wl.sample_rows),
+               "reference": "FP64 direct sum over all columns (rows) for sampled outputs"}
 
     extras = {}
-    if not args.skip_extras and R1 == 1:
+    if not args.skip_extras and R1 == 1 and args.workload == "fio2d":
         # plain FP64 form (middle factor stored: FP64 sincospi on GB300 is slow)
         dp64 = mb.DevicePlan(plan, mb.FP64, mb.S_STORED)
         f64 = f.to(torch.complex128)
@@ -417,7 +516,7 @@ def main():
         del wsR, F, G, H, Gt, Ht, dptc
 
     # end to end through the host-buffer entry point (pinned host memory)
-    fh = torch.from_numpy(synth.complex_gaussian(N, R1, 0).T.astype(np.complex64).copy()).pin_memory()
+    fh = torch.from_numpy(f_host.T.astype(np.complex64).copy()).pin_memory()
     gh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
     hh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
     wsh = torch.empty(dp32.workspace_bytes(R1, host_io=True), dtype=torch.uint8, device=dev)
@@ -437,7 +536,7 @@ def main():
            "d2h_bytes_per_step": 2 * N * R1 * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.skip_extras and R1 == 1:
+    if rank == 0 and ws == 1 and not args.skip_extras and R1 == 1 and args.workload == "fio2d":
         try:
             cpu = cpu_baseline(plan.export(), N)
         except Exception as e:  # the GPU numbers stand without it
@@ -446,15 +545,15 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-           "config": {"workload": f"fio2d_n{n}", "N": N, "d": 2, "phase": "FIO2D closed form",
-                      "nrhs": R1, "mode": args.mode, "step": "forward + adjoint apply", "tol": 1e-6, "n0": 64,
-                      "L": st["L"],
+           "config": {"workload": wl.name, "N": N, "d": wl.d, "phase": PHASE_NAMES.get(wl.phase, str(wl.phase)),
+                      "points": wl.x_kind, "nrhs": R1, "mode": mode_name, "step": "forward + adjoint apply",
+                      "tol": wl.tol, "n0": wl.n0, "L": st["L"], "build": build_site,
                       "t_entries": st["t_entries"], "s_entries": st["s_entries"], "max_rank": st["max_rank"],
                       "mean_rank": round(st["mean_rank"], 1), "factor_bytes": fbytes, "index_bytes": ibytes,
-                      "l2": "flushed (512 MB write) between timed steps; factors 3+ GB > L2",
+                      "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": f"replicas x{ws}", "build_s": round(t_build, 1),
                       "upload_s": round(t_up, 1)},
-           "roofline": roofline, "stages": stage_rows, "clocks": clk, "e2e": e2e,
+           "roofline": roofline, "stages": stage_rows, "rel_l2_direct_sampled": acc, "clocks": clk, "e2e": e2e,
            "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
     out.update(extras)
     if rank == 0:

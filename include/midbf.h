@@ -259,6 +259,16 @@ int midbf_dplan_profile(midbf_dplan* dp, int enable);
 int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kinds, double* bytes,
                       int* n_stages);
 
+/* Size of every stage, in forward order, for flop counts: the stage kind,
+ * the complex entries of the method's factor (the T entries of the
+ * interpolative decompositions V = [I T] Lambda^T of Sec. 3.2, or rows x
+ * columns of the middle-factor blocks of Sec. 3.5) and of the dense blocks
+ * (identity parts included; the blocks the tensor-core modes multiply).
+ * Writes up to max_stages entries of each non-null array and the stage count
+ * to *n_stages.  Host-only; no device work.  EINVAL on a null plan or count. */
+int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t* entries, int64_t* dense,
+                     int* n_stages);
+
 /* midbf_apply_noalloc: midbf_apply for callers that cannot allocate device
  * memory when they apply the operator - for example a service whose GPU
  * memory is entirely owned by another allocator, or a latency-bound loop in

@@ -95,6 +95,8 @@ midbf_dplan_status = _sig("midbf_dplan_status", C.c_int, [_vp, C.c_int, C.POINTE
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
+midbf_stage_info = _sig("midbf_stage_info", C.c_int,
+                        [_vp, C.c_int, C.POINTER(C.c_int), _i64p, _i64p, C.POINTER(C.c_int)])
 midbf_batched_workspace_size = _sig("midbf_batched_workspace_size", C.c_int,
                                     [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_size_t)])
 midbf_apply_batched = _sig("midbf_apply_batched", C.c_int,
@@ -314,6 +316,16 @@ class DevicePlan:
         n = C.c_int()
         check(midbf_stage_times(self.h, 64, ms, kinds, by, C.byref(n)), "midbf_stage_times")
         return [(kinds[i], ms[i], by[i]) for i in range(n.value)]
+
+    def stage_info(self):
+        """[(kind, factor entries, dense entries)] of every stage in forward order."""
+        kinds = (C.c_int * 64)()
+        ent = np.zeros(64, np.int64)
+        den = np.zeros(64, np.int64)
+        n = C.c_int()
+        check(midbf_stage_info(self.h, 64, kinds, ent.ctypes.data_as(_i64p), den.ctypes.data_as(_i64p),
+                               C.byref(n)), "midbf_stage_info")
+        return [(kinds[i], int(ent[i]), int(den[i])) for i in range(n.value)]
 
     # -- torch helpers (device memory and streams come from PyTorch) --------
     def dtype(self):

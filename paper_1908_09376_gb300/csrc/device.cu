@@ -65,6 +65,12 @@ struct DevStage : DevStageBase {
     const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
     const int2* items_cols4 = nullptr;
     int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
+    // tensor-core modes: dense BF16 tile images of the V/U blocks,
+    // [0] forward orientation (stage input -> output), [1] adjoint
+    bool tc = false;
+    TcStage tcs[2]{};
+    int n_tc_items[2] = {0, 0};
+    double tc_bytes[2] = {0, 0};
 };
 
 }  // namespace
@@ -78,6 +84,7 @@ struct midbf_dplan {
     int64_t nx = 0, nw = 0;
     int64_t max_space = 0;        // longest internal vector space
     size_t factor_bytes = 0, index_bytes = 0;
+    size_t tc_image_bytes = 0;    // dense BF16 tile images (tensor-core modes)
     std::vector<void*> allocs;
     std::vector<DevStage<float>> st32;
     std::vector<DevStage<double>> st64;
@@ -87,6 +94,10 @@ struct midbf_dplan {
     std::vector<double> stage_fixed_bytes;
     std::vector<int64_t> stage_vec_entries;
     std::vector<int> stage_kind;
+    // per stage: complex entries of the method's factor (T entries of the IDs,
+    // or rows x cols of the middle-factor blocks) and of the dense blocks
+    // (identity parts of the IDs included)
+    std::vector<int64_t> stage_entries, stage_dense;
     // measurement hooks (midbf_dplan_profile / midbf_stage_times)
     bool profile = false;
     mutable std::vector<cudaEvent_t> ev;
@@ -116,6 +127,115 @@ T* upload(midbf_dplan* dp, const std::vector<T>& v, size_t* counter) {
 inline double frac(double v) { return v - std::nearbyint(v); }
 
 int rows_per_lane(int maxk) { return maxk <= 32 ? 1 : 2; }
+
+// IEEE binary32 -> bfloat16 with round-to-nearest-even on the 16 dropped
+// bits (NaN stays a quiet NaN).
+uint16_t bf16_bits(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40u);
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Dense tile images of the blocks of a V or U stage for k_blk_tc.
+//
+// Per block, G is the narrow x wide matrix of its interpolative
+// decompositions (Sec. 3.2): row c of sub-block s has a one in the column of
+// its skeleton skel_c and T_s(c, r) in the column of redundant index red_r.
+// The oriented matrices are
+//   V stage: forward G,   adjoint G^H;
+//   U stage: forward G^T, adjoint conj(G),
+// each cut into 128-row x 32-column tiles whose BF16 images (hi, then lo in
+// the refined mode) are laid out as the core-matrix operand of the MMA.
+template <class R>
+void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
+    const bool is_v = st.kind == KIND_V;
+    const int NP = dp->tc_mode == 2 ? 2 : 1;
+    const int nb = (int)st.blocks.size();
+    for (int o = 0; o < 2; ++o) {
+        std::vector<TcBlock> tb(nb);
+        std::vector<int> ipos, opos;
+        std::vector<int2> items;
+        long long off = 0;
+        for (int b = 0; b < nb; ++b) {
+            const Block& bk = st.blocks[b];
+            const std::vector<int64_t>& src = o == 0 ? bk.in_idx : bk.out_idx;
+            const std::vector<int64_t>& dst = o == 0 ? bk.out_idx : bk.in_idx;
+            TcBlock& t = tb[b];
+            t.rows = (int)dst.size();
+            t.cols = (int)src.size();
+            t.in_off = (int)ipos.size();
+            t.out_off = (int)opos.size();
+            t.img_off = off;
+            for (int64_t v : src) ipos.push_back((int)v);
+            for (int64_t v : dst) opos.push_back((int)v);
+            const int nrt = (t.rows + kTcM - 1) / kTcM, nch = (t.cols + kTcCols - 1) / kTcCols;
+            for (int r = 0; r < nrt; ++r) items.push_back(make_int2(b, r));
+            off += (long long)nrt * nch * NP * kTcTileElems;
+        }
+        std::vector<uint16_t> img((size_t)off, 0);
+        auto fill = [&](int b) {
+            const Block& bk = st.blocks[b];
+            const TcBlock& t = tb[b];
+            const int nch = (t.cols + kTcCols - 1) / kTcCols;
+            auto put = [&](int i, int j, float re, float im) {
+                const int rt = i / kTcM, r = i % kTcM, c = j / kTcCols, jj = j % kTcCols;
+                uint16_t* tile = &img[(size_t)t.img_off + ((size_t)rt * nch + c) * NP * kTcTileElems];
+                const float v[2] = {re, im};
+                for (int q = 0; q < 2; ++q) {
+                    const int k = 2 * jj + q;
+                    const size_t e = (size_t)(((r >> 3) * (kTcK >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7));
+                    const uint16_t hi = bf16_bits(v[q]);
+                    tile[e] = hi;
+                    if (NP == 2) tile[kTcTileElems + e] = bf16_bits(v[q] - bf16_value(hi));
+                }
+            };
+            // (narrow row, wide column, value of G) -> entry of the oriented matrix
+            auto emit = [&](int nrow, int wcol, cplx g) {
+                const float re = (float)g.real(), im = (float)g.imag();
+                if (is_v) {
+                    if (o == 0) put(nrow, wcol, re, im);
+                    else put(wcol, nrow, re, -im);
+                } else {
+                    if (o == 0) put(wcol, nrow, re, im);
+                    else put(nrow, wcol, re, -im);
+                }
+            };
+            int noff = 0;
+            for (const Sub& sb : bk.subs) {
+                const int nred = sb.m - sb.k;
+                for (int c = 0; c < sb.k; ++c) {
+                    emit(noff + c, sb.skel[c], cplx(1.0, 0.0));
+                    for (int r = 0; r < nred; ++r) emit(noff + c, sb.red[r], sb.T[(size_t)c * nred + r]);
+                }
+                noff += sb.k;
+            }
+        };
+        const int nthreads = std::max(1u, std::thread::hardware_concurrency());
+        std::vector<std::thread> th;
+        for (int w = 0; w < nthreads; ++w)
+            th.emplace_back([&, w]() {
+                for (int b = w; b < nb; b += nthreads) fill(b);
+            });
+        for (auto& t : th) t.join();
+        ds.tcs[o].blocks = upload(dp, tb, &dp->index_bytes);
+        ds.tcs[o].in_pos = upload(dp, ipos, &dp->index_bytes);
+        ds.tcs[o].out_pos = upload(dp, opos, &dp->index_bytes);
+        ds.tcs[o].items = upload(dp, items, &dp->index_bytes);
+        ds.tcs[o].img = reinterpret_cast<const __nv_bfloat16*>(upload(dp, img, &dp->tc_image_bytes));
+        ds.n_tc_items[o] = (int)items.size();
+        ds.tc_bytes[o] = (double)img.size() * 2.0;
+    }
+    ds.tc = true;
+}
 
 // Build the device arrays of an ID stage (V or U), or of a stored S stage
 // seen as dense blocks with no skeleton.
@@ -229,6 +349,9 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     ds.ids1 = ds.ids;
     ds.ids1.items_c = upload(dp, items_c1, &dp->index_bytes);
     ds.n_items_c1 = (int)items_c1.size();
+    if constexpr (sizeof(R) == 4) {
+        if (dp->tc_mode && !stored_s) make_tc_images<R>(dp, st, ds);
+    }
 }
 
 // Split of the phase for one S block (see kernels.cuh): rows get (a, u, C),
@@ -421,6 +544,20 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out)
         dp->stage_fixed_bytes.push_back((double)(dp->factor_bytes - f0) + (double)(dp->index_bytes - i0));
         dp->stage_vec_entries.push_back(in_len + st.out_len);
         dp->stage_kind.push_back(st.kind);
+        int64_t ent = 0, dense = 0;
+        for (const Block& bk : st.blocks) {
+            if (st.kind == KIND_S) {
+                ent += (int64_t)bk.xidx.size() * (int64_t)bk.widx.size();
+                dense += (int64_t)bk.xidx.size() * (int64_t)bk.widx.size();
+            } else {
+                for (const Sub& sb : bk.subs) {
+                    ent += (int64_t)sb.k * (sb.m - sb.k);
+                    dense += (int64_t)sb.k * sb.m;
+                }
+            }
+        }
+        dp->stage_entries.push_back(ent);
+        dp->stage_dense.push_back(dense);
         if (!ds.in_user) dp->max_space = std::max(dp->max_space, in_len);
         if (!ds.out_user) dp->max_space = std::max(dp->max_space, st.out_len);
         in_len = st.out_len;
@@ -599,7 +736,8 @@ void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
     CK(cudaGetLastError());
 }
 
-constexpr int kTcMinRhs = 16;  // tensor cores for the middle factor from this many RHS on
+constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
+constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
 
 template <int PQ, bool RF, bool CJ>
 void launch_tc_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
@@ -642,6 +780,24 @@ void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, 
     CK(cudaGetLastError());
 }
 
+template <bool RF>
+void launch_blk_tc_t(const TcStage& st, int items, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
+                     cudaStream_t s) {
+    const size_t sm = tcb_smem_bytes<RF>();
+    auto kf = k_blk_tc<RF>;
+    set_smem(kf, sm);
+    kf<<<items, kTcThreads, sm, s>>>(st, src, dst, nrhs, status);
+}
+
+// V / U stage on the tensor cores: o = 0 forward, 1 adjoint orientation.
+void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<float> dst, int nrhs, bool refine,
+                   int* status, cudaStream_t s) {
+    if (ds.n_tc_items[o] == 0) return;
+    if (refine) launch_blk_tc_t<true>(ds.tcs[o], ds.n_tc_items[o], src, dst, nrhs, status, s);
+    else launch_blk_tc_t<false>(ds.tcs[o], ds.n_tc_items[o], src, dst, nrhs, status, s);
+    CK(cudaGetLastError());
+}
+
 template <class R>
 int count_launches(const std::vector<DevStage<R>>& st) {
     int n = 0;
@@ -679,7 +835,15 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
         VecRef<R> fout = ds.out_user ? (adjoint ? uin : uout) : internal(sidx);
         VecRef<R> src = adjoint ? fout : fin;
         VecRef<R> dst = adjoint ? fin : fout;
-        if (ds.id) {
+        bool tc_done = false;
+        if constexpr (sizeof(R) == 4) {
+            if (ds.id && ds.tc && nrhs >= kTcBlkMinRhs) {
+                launch_blk_tc(ds, adjoint ? 1 : 0, src, dst, nrhs, dp->tc_mode == 2, dp->d_status, s);
+                tc_done = true;
+            }
+        }
+        if (tc_done) {
+        } else if (ds.id) {
             const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
             // pattern R computes narrow from wide; pattern C wide from narrow.
             const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
@@ -1027,6 +1191,22 @@ int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kin
         set_last_error(e.what());
         return e.code;
     }
+}
+
+int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t* entries, int64_t* dense,
+                     int* n_stages) {
+    if (!dp || !n_stages || max_stages < 0) {
+        set_last_error("midbf_stage_info: bad argument");
+        return MIDBF_EINVAL;
+    }
+    const int ns = (int)dp->stage_kind.size();
+    for (int q = 0; q < ns && q < max_stages; ++q) {
+        if (kinds) kinds[q] = dp->stage_kind[q];
+        if (entries) entries[q] = dp->stage_entries[q];
+        if (dense) dense[q] = dp->stage_dense[q];
+    }
+    *n_stages = ns;
+    return MIDBF_OK;
 }
 
 int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, void* out, int64_t ldout,

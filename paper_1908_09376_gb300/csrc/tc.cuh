@@ -101,10 +101,10 @@ template <int PQ, bool REFINE, bool CONJ>
 __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<float> rs, SSide<float> cs,
                                                         VecRef<float> src, VecRef<float> dst, int nrhs,
                                                         int row_is_row, int* status) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     using Sh = PhaseShape<PQ>;
     constexpr int NP = REFINE ? 2 : 1;
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);                 // [stage][part][128*64]
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);                 // [stage][part][128*64]
     __nv_bfloat16* sB = sA + 2 * NP * kTcM * kTcK;                                    // [stage][part][256*64]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 2 * NP * 2 * kTcMaxR * kTcK);  // [2]
     uint32_t* taddr = reinterpret_cast<uint32_t*>(mbar + 2);
@@ -385,9 +385,9 @@ __host__ __device__ constexpr size_t tcb_smem_bytes() {
 template <bool REFINE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, VecRef<float> src, VecRef<float> dst, int nrhs,
                                                           int* status) {
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     constexpr int NP = REFINE ? 2 : 1;
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(smem_raw);                 // [stage][part][128*64]
+    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);                 // [stage][part][128*64]
     __nv_bfloat16* sB = sA + 2 * NP * kTcM * kTcK;                                    // [stage][part][256*64]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 2 * NP * 2 * kTcMaxR * kTcK);  // [2] MMA done
     uint64_t* fbar = mbar + 2;                                                        // [2] A tile landed
@@ -525,6 +525,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, VecRef<flo
                                "=r"(v[7])
                              : "r"(addr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (nchunk == 0) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = 0u;   // empty input side: the product is zero
+                }
                 if (ii < bk.rows) {
                     const int op = st.out_pos[bk.out_off + ii];
 #pragma unroll
