@@ -49,18 +49,25 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--n", type=int, default=None, help="grid size of the 2D workloads")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
-    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump_n1024"],
-                    help="fio2d: 2D FIO phase on the n x n grid (--n); fio3d_n32: 3D, N = 32,768, random X; "
-                         "fio2d_jump_n1024: 2D with the jump |xi| sign(x1 - 1/2), N = 1,048,576")
+    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump"],
+                    help="fio2d: 2D FIO phase on the n x n grid (--n, default 256); fio3d_n32: 3D, N = 32,768, "
+                         "random X; fio2d_jump: 2D with the jump |xi| sign(x1 - 1/2) (--n, default 1024)")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's)")
     ap.add_argument("--mode", default=None, choices=["fp32", "bf16", "bf16r"],
                     help="arithmetic: complex FP32, or BF16 tensor cores with FP32 accumulation "
                          "(bf16r: with the refinement products); default fp32, bf16r for fio3d_n32")
     ap.add_argument("--build", default=None, choices=["host", "device"],
                     help="where the interpolative decompositions run (default: host for fio2d, else device)")
+    ap.add_argument("--tune", default=None, choices=["on", "off"],
+                    help="run the autotuner for the RHS count before timing (default: on for fio2d_jump)")
+    ap.add_argument("--graph", default=None, choices=["on", "off"],
+                    help="time the step as one CUDA-graph replay (default: on for fio2d_jump)")
+    ap.add_argument("--store", default=None, choices=["fp64", "fp32"],
+                    help="host storage of the IDs' coefficients (default fp64; fp32 for fio2d_jump, whose "
+                         "n = 1024 plan does not fit host memory in FP64)")
     return ap.parse_args()
 
 
@@ -98,14 +105,23 @@ def workload(n):
 def pick_workload(args):
     """The synthetic workload, its RHS count, arithmetic and build site."""
     if args.workload == "fio2d":
-        w = synth.Workload(f"fio2d_n{args.n}", 2, args.n, synth.PHASE_FIO2D, 1e-6, 64, 1, 0,
-                           sample_rows=256, sample_seed=3)
+        n = args.n or 256
+        w = synth.Workload(f"fio2d_n{n}", 2, n, synth.PHASE_FIO2D, 1e-6, 64, 1, 0, sample_rows=256, sample_seed=3)
+    elif args.workload == "fio2d_jump":
+        base = synth.WORKLOADS["fio2d_jump_n1024"]
+        n = args.n or base.n
+        w = synth.Workload(f"fio2d_jump_n{n}", 2, n, base.phase, base.tol, base.n0, base.nrhs, base.f_seed,
+                           sample_rows=base.sample_rows, sample_seed=base.sample_seed)
     else:
         w = synth.WORKLOADS[args.workload]
     nrhs = args.nrhs if args.nrhs is not None else w.nrhs
     mode = args.mode if args.mode is not None else ("bf16r" if w.d == 3 else "fp32")
     build = args.build if args.build is not None else ("host" if args.workload == "fio2d" else "device")
-    return w, nrhs, mode, build
+    store = args.store if args.store is not None else ("fp32" if args.workload == "fio2d_jump" else "fp64")
+    jump = args.workload == "fio2d_jump"
+    tune = (args.tune or ("on" if jump else "off")) == "on"
+    graph = (args.graph or ("on" if jump else "off")) == "on"
+    return w, nrhs, mode, build, store, tune, graph
 
 
 PHASE_NAMES = {synth.PHASE_FIO2D: "FIO2D closed form", synth.PHASE_FIO3D: "FIO3D closed form",
@@ -269,12 +285,13 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     import paper_1908_09376_gb300 as mb
-    X, W, bx, bw = workload(args.n)
+    n = args.n or 256
+    X, W, bx, bw = workload(n)
     plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=64, boxX=bx, boxW=bw,
                          nthreads=args.threads)
     smp = OracleSample(plan.export())
     del plan
-    N = args.n ** 2
+    N = n ** 2
     for _ in range(args.warmup):
         smp.step_seconds()
     times = [smp.step_seconds() for _ in range(args.steps)]
@@ -284,7 +301,7 @@ def run_reference(args, ws, rank):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points*RHS/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": f"fio2d_n{args.n}", "N": N, "nrhs": 1, "tol": 1e-6, "n0": 64,
+           "config": {"workload": f"fio2d_n{n}", "N": N, "nrhs": 1, "tol": 1e-6, "n0": 64,
                       "step": "forward + adjoint apply"},
            "cpu_baseline": cpu, "e2e": {"value": v, "unit": "points*RHS/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
@@ -306,7 +323,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    wl, R1, mode_name, build_site = pick_workload(args)
+    wl, R1, mode_name, build_site, store, tune, use_graph = pick_workload(args)
     n = wl.n
     N = wl.N
     X, W, bx, bw = wl.points()
@@ -314,7 +331,7 @@ def main():
     t0 = time.perf_counter()
     ph = mb.Phase.closed_form(wl.phase, X, W)
     plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads,
-                         device_ids=1 if build_site == "device" else 0)
+                         device_ids=1 if build_site == "device" else 0, store_fp32=1 if store == "fp32" else 0)
     t_build = time.perf_counter() - t0
     st = plan.stats()
     t0 = time.perf_counter()
@@ -335,9 +352,28 @@ def main():
     stream = torch.cuda.current_stream(dev)
     launches_per_apply = dp32.launches()
 
-    def step():
+    t_tune = 0.0
+    if tune:
+        t0 = time.perf_counter()
+        dp32.autotune(R1)
+        t_tune = time.perf_counter() - t0
+
+    def step_direct():
         dp32.apply(f, out=g, workspace=ws1)
         dp32.apply(g, adjoint=True, out=h, workspace=ws1)
+
+    step = step_direct
+    if use_graph:
+        # the forward + adjoint step recorded once, replayed as one graph launch
+        cs = torch.cuda.Stream(dev)
+        cs.wait_stream(stream)
+        with mb.capture(cs, keep=(f, g, h, ws1)) as cap:
+            dp32.apply(f, out=g, workspace=ws1, stream=cs)
+            dp32.apply(g, adjoint=True, out=h, workspace=ws1, stream=cs)
+        step_graph = cap.graph
+
+        def step():
+            step_graph.launch(stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -547,7 +583,10 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
            "config": {"workload": wl.name, "N": N, "d": wl.d, "phase": PHASE_NAMES.get(wl.phase, str(wl.phase)),
                       "points": wl.x_kind, "nrhs": R1, "mode": mode_name, "step": "forward + adjoint apply",
-                      "tol": wl.tol, "n0": wl.n0, "L": st["L"], "build": build_site,
+                      "tol": wl.tol, "n0": wl.n0, "L": st["L"], "build": build_site, "store": store,
+                      "autotuned": tune, "tune_s": round(t_tune, 1), "cuda_graph": use_graph,
+                      "choices": ([[dp32.choice(R1, q, 0), dp32.choice(R1, q, 1)] for q in range(len(sinfo))]
+                                  if tune else None),
                       "t_entries": st["t_entries"], "s_entries": st["s_entries"], "max_rank": st["max_rank"],
                       "mean_rank": round(st["mean_rank"], 1), "factor_bytes": fbytes, "index_bytes": ibytes,
                       "l2": "flushed (512 MB write) between timed steps",

@@ -152,6 +152,11 @@ typedef struct {
     double boxW[4];
     int device_ids;    /* 1: kernel samples and pivoted QRs on the current CUDA
                           device (FP64), 0: on the host threads               */
+    int store_fp32;    /* 1: keep the ID coefficients T of the built plan in
+                          complex FP32 on the host (half the memory; the QRs
+                          still run in FP64, and T's rounding, 6e-8 relative,
+                          is far below the ID tolerance); export writes FP64.
+                          0: complex FP64                                      */
 } midbf_params;
 
 int midbf_params_default(int d, midbf_params* p);
@@ -244,6 +249,66 @@ int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adj
                         const void* const* in, const int64_t* ldin, void* const* out,
                         const int64_t* ldout, const int* nrhs, void* stream,
                         void* workspace, size_t workspace_bytes);
+
+/* ---- CUDA graphs ----------------------------------------------------------
+ * A sequence of midbf_apply / midbf_apply_batched / midbf_apply_noalloc
+ * calls issued on one stream can be recorded once and replayed with one
+ * launch: midbf_capture_begin(stream), the apply calls on that stream, then
+ * midbf_capture_end(stream, &graph); midbf_graph_launch(graph, s) replays
+ * the whole sequence on any stream s of the same device, any number of
+ * times.  A replay reads and writes the very buffers and workspaces named
+ * in the recorded calls, with the same nrhs: their contents may change
+ * between replays, their addresses may not, and they must stay allocated
+ * while the graph exists.  The apply calls issue no allocation,
+ * synchronization or host copy, so they record as kernel nodes only
+ * (midbf_apply_host cannot be recorded; it returns MIDBF_EINVAL while its
+ * stream records).  Profiling (midbf_dplan_profile) must be off for every
+ * plan applied while recording.  The recording is thread-local: other
+ * threads keep their ordinary CUDA behaviour.
+ * Errors: MIDBF_EINVAL for a null or legacy-default stream, a null output,
+ * or midbf_capture_end without a recording in progress; MIDBF_ECUDA when
+ * CUDA refuses the capture or the instantiation (the recording is then
+ * ended and discarded). */
+typedef struct midbf_graph midbf_graph;
+int midbf_capture_begin(void* stream);
+int midbf_capture_end(void* stream, midbf_graph** graph);
+int midbf_graph_launch(const midbf_graph* graph, void* stream);
+void midbf_graph_destroy(midbf_graph* graph);
+
+/* ---- kernel choices and the autotuner ------------------------------------
+ * Every stage of an apply runs one kernel variant.  By default the library
+ * picks it by fixed rules: the tensor-core kernels in the MIDBF_BF16 modes
+ * from 16 RHS on, else the SIMT kernel with the smallest RHS tile that covers
+ * nrhs (at most 16 in FP32, 8 in FP64) and fits shared memory, one CTA per
+ * work item.  A choice per (nrhs, stage, direction) overrides the rules:
+ *   MIDBF_CHOICE_DEFAULT  the rules;
+ *   1, 2, 4, 8, 16        the SIMT kernel with this RHS tile (taken when it
+ *                         fits shared memory; else the rules' tile);
+ *   MIDBF_CHOICE_COLUMN1  the one-RHS column kernel of a U stage forward or a
+ *                         V stage adjoint (nrhs = 1 only; else the rules);
+ *   any of the above | MIDBF_CHOICE_PERSIST
+ *                         the same SIMT kernel launched persistent: as many
+ *                         CTAs as are resident on the GPU at once, each
+ *                         looping over the level's work items;
+ *   MIDBF_CHOICE_TENSOR   the tensor-core kernel (BF16 modes only; else the
+ *                         rules).
+ * midbf_autotune times every applicable variant of every stage in both
+ * directions for nrhs right-hand sides on `stream` and records the fastest;
+ * later applies with that nrhs use it (midbf_apply_batched uses the SIMT
+ * tiles).  It allocates and frees temporary device vectors, waits for the
+ * stream, and must not run concurrently with applies of the same dplan or
+ * while the stream records a graph.  midbf_set_choice records a choice by
+ * hand, midbf_get_choice reads the one in force.  stage: index in forward
+ * order (0 .. midbf_stage_info's count - 1).
+ * Errors: MIDBF_EINVAL (bad arguments or an unknown choice), MIDBF_ENOMEM,
+ * MIDBF_ECUDA, MIDBF_ETIMEOUT (a tensor-core wait gave up while tuning). */
+#define MIDBF_CHOICE_DEFAULT 0
+#define MIDBF_CHOICE_COLUMN1 32
+#define MIDBF_CHOICE_PERSIST 256
+#define MIDBF_CHOICE_TENSOR 1024
+int midbf_autotune(midbf_dplan* dp, int nrhs, void* stream);
+int midbf_set_choice(midbf_dplan* dp, int nrhs, int stage, int adjoint, int choice);
+int midbf_get_choice(const midbf_dplan* dp, int nrhs, int stage, int adjoint, int* choice);
 
 /* Number of kernel launches one midbf_apply issues (for launch accounting). */
 int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches);

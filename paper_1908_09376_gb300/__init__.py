@@ -23,6 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 # ---- constants (include/midbf.h) ------------------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ECALLBACK, ERANK, ERECOVERY, ETIMEOUT, EINTERNAL, EFORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
+CHOICE_DEFAULT, CHOICE_COLUMN1, CHOICE_PERSIST, CHOICE_TENSOR = 0, 32, 256, 1024
 PHASE_FIO2D, PHASE_FIO3D, PHASE_FIO2D_JUMP, PHASE_DOT, PHASE_ZERO, PHASE_SEPARABLE, PHASE_LOWRANK = 1, 2, 3, 4, 5, 6, 7
 FP64, FP32, BF16, REFINE = 0, 1, 2, 16
 S_ONTHEFLY, S_STORED = 0, 1
@@ -35,7 +36,8 @@ _vp = C.c_void_p
 class midbf_params(C.Structure):
     _fields_ = [("tol", C.c_double), ("n0", C.c_int), ("t", C.c_double), ("kest", C.c_int),
                 ("kmax", C.c_int), ("seed", C.c_uint64), ("nthreads", C.c_int), ("use_box", C.c_int),
-                ("boxX", C.c_double * 4), ("boxW", C.c_double * 4), ("device_ids", C.c_int)]
+                ("boxX", C.c_double * 4), ("boxW", C.c_double * 4), ("device_ids", C.c_int),
+                ("store_fp32", C.c_int)]
 
 
 class midbf_stats(C.Structure):
@@ -95,6 +97,13 @@ midbf_dplan_status = _sig("midbf_dplan_status", C.c_int, [_vp, C.c_int, C.POINTE
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
+midbf_autotune = _sig("midbf_autotune", C.c_int, [_vp, C.c_int, _vp])
+midbf_set_choice = _sig("midbf_set_choice", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int])
+midbf_get_choice = _sig("midbf_get_choice", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)])
+midbf_capture_begin = _sig("midbf_capture_begin", C.c_int, [_vp])
+midbf_capture_end = _sig("midbf_capture_end", C.c_int, [_vp, C.POINTER(_vp)])
+midbf_graph_launch = _sig("midbf_graph_launch", C.c_int, [_vp, _vp])
+midbf_graph_destroy = _sig("midbf_graph_destroy", None, [_vp])
 midbf_stage_info = _sig("midbf_stage_info", C.c_int,
                         [_vp, C.c_int, C.POINTER(C.c_int), _i64p, _i64p, C.POINTER(C.c_int)])
 midbf_batched_workspace_size = _sig("midbf_batched_workspace_size", C.c_int,
@@ -317,6 +326,20 @@ class DevicePlan:
         check(midbf_stage_times(self.h, 64, ms, kinds, by, C.byref(n)), "midbf_stage_times")
         return [(kinds[i], ms[i], by[i]) for i in range(n.value)]
 
+    def autotune(self, nrhs, stream=None):
+        """Time every kernel variant of every stage for nrhs RHS and keep the fastest."""
+        import torch
+        s = torch.cuda.current_stream() if stream is None else stream
+        check(midbf_autotune(self.h, nrhs, C.c_void_p(s.cuda_stream)), "midbf_autotune")
+
+    def set_choice(self, nrhs, stage, adjoint, choice):
+        check(midbf_set_choice(self.h, nrhs, stage, int(adjoint), choice), "midbf_set_choice")
+
+    def choice(self, nrhs, stage, adjoint):
+        c = C.c_int()
+        check(midbf_get_choice(self.h, nrhs, stage, int(adjoint), C.byref(c)), "midbf_get_choice")
+        return c.value
+
     def stage_info(self):
         """[(kind, factor entries, dense entries)] of every stage in forward order."""
         kinds = (C.c_int * 64)()
@@ -370,6 +393,55 @@ class DevicePlan:
         check(midbf_apply_host(self.h, int(adjoint), xs.ctypes.data, out.ctypes.data, nrhs, s.cuda_stream,
                                workspace.data_ptr(), workspace.numel()), "midbf_apply_host")
         return out.reshape(-1) if vec else out
+
+
+class Graph:
+    """A recorded sequence of apply calls (midbf_capture_begin/_end), replayed
+    with one launch.  The buffers named in the recorded calls must outlive it."""
+
+    def __init__(self, handle, keep):
+        self.h = handle
+        self._keep = keep
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            midbf_graph_destroy(self.h)
+            self.h = None
+
+    def launch(self, stream=None):
+        import torch
+        s = stream or torch.cuda.current_stream()
+        check(midbf_graph_launch(self.h, C.c_void_p(s.cuda_stream)), "midbf_graph_launch")
+
+
+class capture:
+    """Context manager recording the apply calls issued on `stream` (a
+    non-default torch.cuda.Stream, made current inside the block) into a
+    Graph, available as .graph after the block.  `keep` holds references to
+    the tensors the recorded calls use."""
+
+    def __init__(self, stream, keep=()):
+        self.stream = stream
+        self.keep = list(keep)
+        self.graph = None
+
+    def __enter__(self):
+        import torch
+        self._ctx = torch.cuda.stream(self.stream)
+        self._ctx.__enter__()
+        check(midbf_capture_begin(C.c_void_p(self.stream.cuda_stream)), "midbf_capture_begin")
+        return self
+
+    def __exit__(self, et, ev, tb):
+        h = _vp()
+        rc = midbf_capture_end(C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        self._ctx.__exit__(et, ev, tb)
+        if et is None:
+            check(rc, "midbf_capture_end")
+            self.graph = Graph(h, self.keep)
+        elif rc == OK:
+            midbf_graph_destroy(h)
+        return False
 
 
 def apply_batched(dplans, xs, adjoints, outs=None, workspace=None, stream=None):

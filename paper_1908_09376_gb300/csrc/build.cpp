@@ -409,6 +409,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
                 o.sub.skel = r.skel;
                 o.sub.red = r.red;
                 o.sub.T = std::move(r.T);
+                if (prm.store_fp32) o.sub.to_fp32();
                 o.skel_pts.resize(k);
                 for (int64_t i = 0; i < k; ++i) o.skel_pts[i] = cols[r.skel[i]];
                 return o;
@@ -478,6 +479,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
                     o.sub.skel = std::move(rep[q].skel);
                     o.sub.red = std::move(rep[q].red);
                     o.sub.T = std::move(rep[q].T);
+                    if (prm.store_fp32) o.sub.to_fp32();
                     o.skel_pts.resize(k);
                     for (int64_t i = 0; i < k; ++i) o.skel_pts[i] = colsv[e][o.sub.skel[i]];
                     done[e] = 1;

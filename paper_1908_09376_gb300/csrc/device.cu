@@ -19,6 +19,7 @@
 #include <type_traits>
 #include <numeric>
 #include <thread>
+#include <tuple>
 
 #include "internal.hpp"
 #include "kernels.cuh"
@@ -98,6 +99,8 @@ struct midbf_dplan {
     // or rows x cols of the middle-factor blocks) and of the dense blocks
     // (identity parts of the IDs included)
     std::vector<int64_t> stage_entries, stage_dense;
+    // kernel choices per RHS count: [stage][0 forward, 1 adjoint] (midbf_autotune)
+    std::map<int, std::vector<std::array<int, 2>>> tuned;
     // measurement hooks (midbf_dplan_profile / midbf_stage_times)
     bool profile = false;
     mutable std::vector<cudaEvent_t> ev;
@@ -153,8 +156,9 @@ float bf16_value(uint16_t h) {
 // The oriented matrices are
 //   V stage: forward G,   adjoint G^H;
 //   U stage: forward G^T, adjoint conj(G),
-// each cut into 128-row x 32-column tiles whose BF16 images (hi, then lo in
-// the refined mode) are laid out as the core-matrix operand of the MMA.
+// each cut into 128-row x 16-column tiles.  A tile image holds the real
+// embedding row (Re a, -Im a) of every entry a, interleaved along K, as BF16
+// (hi, then lo in the refined mode) in the core-matrix layout of the MMA.
 template <class R>
 void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
     const bool is_v = st.kind == KIND_V;
@@ -177,7 +181,7 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
             t.img_off = off;
             for (int64_t v : src) ipos.push_back((int)v);
             for (int64_t v : dst) opos.push_back((int)v);
-            const int nrt = (t.rows + kTcM - 1) / kTcM, nch = (t.cols + kTcCols - 1) / kTcCols;
+            const int nrt = (t.rows + kTcM - 1) / kTcM, nch = (t.cols + kTcKc - 1) / kTcKc;
             for (int r = 0; r < nrt; ++r) items.push_back(make_int2(b, r));
             off += (long long)nrt * nch * NP * kTcTileElems;
         }
@@ -185,14 +189,13 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
         auto fill = [&](int b) {
             const Block& bk = st.blocks[b];
             const TcBlock& t = tb[b];
-            const int nch = (t.cols + kTcCols - 1) / kTcCols;
+            const int nch = (t.cols + kTcKc - 1) / kTcKc;
             auto put = [&](int i, int j, float re, float im) {
-                const int rt = i / kTcM, r = i % kTcM, c = j / kTcCols, jj = j % kTcCols;
+                const int rt = i / kTcM, r = i % kTcM, c = j / kTcKc, jj = j % kTcKc;
                 uint16_t* tile = &img[(size_t)t.img_off + ((size_t)rt * nch + c) * NP * kTcTileElems];
-                const float v[2] = {re, im};
+                const float v[2] = {re, -im};
                 for (int q = 0; q < 2; ++q) {
-                    const int k = 2 * jj + q;
-                    const size_t e = (size_t)(((r >> 3) * (kTcK >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7));
+                    const size_t e = (size_t)core_off(r, 2 * jj + q, kTcK);
                     const uint16_t hi = bf16_bits(v[q]);
                     tile[e] = hi;
                     if (NP == 2) tile[kTcTileElems + e] = bf16_bits(v[q] - bf16_value(hi));
@@ -214,7 +217,7 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
                 const int nred = sb.m - sb.k;
                 for (int c = 0; c < sb.k; ++c) {
                     emit(noff + c, sb.skel[c], cplx(1.0, 0.0));
-                    for (int r = 0; r < nred; ++r) emit(noff + c, sb.red[r], sb.T[(size_t)c * nred + r]);
+                    for (int r = 0; r < nred; ++r) emit(noff + c, sb.red[r], sb.t((size_t)c * nred + r));
                 }
                 noff += sb.k;
             }
@@ -309,7 +312,7 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
                 for (int jj = 0; jj < nred; ++jj) red.push_back(sb.red[perm[jj]]);
                 for (int jj = 0; jj < nred; ++jj)
                     for (int i = 0; i < sb.k; ++i) {
-                        const cplx& v = sb.T[(size_t)i * nred + perm[jj]];
+                        const cplx v = sb.t((size_t)i * nred + perm[jj]);
                         T.push_back({(R)v.real(), (R)v.imag()});
                     }
                 subs.push_back(sd);
@@ -596,89 +599,126 @@ int pick_nr(int nrhs, const std::function<size_t(int)>& smem) {
     return nr;
 }
 
+// Grid of a SIMT launch: one CTA per work item, or (persistent) as many CTAs
+// as are resident on the GPU at once, each looping over the items with the
+// grid size as stride (the kernels' item loops).
+int grid_for(const void* kernel, size_t smem, int nitems, bool persist) {
+    if (!persist || nitems <= 0) return nitems;
+    static std::mutex mu;
+    static std::map<std::tuple<const void*, size_t, int>, int> cache;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const auto key = std::make_tuple(kernel, smem, dev);
+    {
+        std::lock_guard<std::mutex> g(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return std::min(nitems, it->second);
+    }
+    int per_sm = 0, nsm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, reinterpret_cast<const void*>(kernel), kThreads, smem));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int cap = std::max(1, per_sm) * std::max(1, nsm);
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = cap;
+    return std::min(nitems, cap);
+}
+
 template <class R, int RT, int NR, bool CJ>
-void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
     const size_t sm = pattern_r_smem<R>(ds.max_nred, RT, NR);
     auto kf = k_pattern_r<R, RT, NR, CJ>;
     set_smem(kf, sm);
-    kf<<<ds.n_items_r, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+    const int n = ds.n_items_r;
+    kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
 }
 
 template <class R, int RT, bool CJ>
-void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     switch (nr) {
-        case 1: launch_r_t<R, RT, 1, CJ>(ds, src, dst, nrhs, s); break;
-        case 2: launch_r_t<R, RT, 2, CJ>(ds, src, dst, nrhs, s); break;
-        case 4: launch_r_t<R, RT, 4, CJ>(ds, src, dst, nrhs, s); break;
-        case 8: launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s); break;
+        case 1: launch_r_t<R, RT, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 2: launch_r_t<R, RT, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 4: launch_r_t<R, RT, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 8: launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
         default:
-            if constexpr (sizeof(R) == 4) launch_r_t<R, RT, 16, CJ>(ds, src, dst, nrhs, s);
-            else launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s);
+            if constexpr (sizeof(R) == 4) launch_r_t<R, RT, 16, CJ>(ds, src, dst, nrhs, s, persist);
+            else launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist);
     }
 }
 
+// A forced RHS tile (from the autotuner) is taken when it is one of the
+// compiled tiles and fits the shared-memory budget; otherwise pick_nr decides.
 template <class R>
-void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
+int forced_or_pick(int force, int nrhs, const std::function<size_t(int)>& smem) {
+    const int cap = sizeof(R) == 4 ? 16 : 8;
+    if (force > 0 && force <= cap && (force & (force - 1)) == 0 && smem(force) <= kSmemCap) return force;
+    return pick_nr<R>(nrhs, smem);
+}
+
+template <class R>
+void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
+              bool persist = false) {
     if (ds.n_items_r == 0) return;
-    const int nr = pick_nr<R>(nrhs, [&](int q) { return pattern_r_smem<R>(ds.max_nred, ds.rt, q); });
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_r_smem<R>(ds.max_nred, ds.rt, q); });
     if (ds.rt == 1) {
-        if (conj) launch_r_nr<R, 1, true>(ds, src, dst, nrhs, nr, s);
-        else launch_r_nr<R, 1, false>(ds, src, dst, nrhs, nr, s);
+        if (conj) launch_r_nr<R, 1, true>(ds, src, dst, nrhs, nr, s, persist);
+        else launch_r_nr<R, 1, false>(ds, src, dst, nrhs, nr, s, persist);
     } else {
-        if (conj) launch_r_nr<R, 2, true>(ds, src, dst, nrhs, nr, s);
-        else launch_r_nr<R, 2, false>(ds, src, dst, nrhs, nr, s);
+        if (conj) launch_r_nr<R, 2, true>(ds, src, dst, nrhs, nr, s, persist);
+        else launch_r_nr<R, 2, false>(ds, src, dst, nrhs, nr, s, persist);
     }
     CK(cudaGetLastError());
 }
 
 template <class R, int NR, bool CJ>
-void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
     const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, NR);
     auto kf = k_pattern_c<R, NR, CJ>;
     set_smem(kf, sm);
-    kf<<<ds.n_items_c, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+    const int n = ds.n_items_c;
+    kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
 }
 
 template <class R, bool CJ>
-void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     switch (nr) {
-        case 1: launch_c_t<R, 1, CJ>(ds, src, dst, nrhs, s); break;
-        case 2: launch_c_t<R, 2, CJ>(ds, src, dst, nrhs, s); break;
-        case 4: launch_c_t<R, 4, CJ>(ds, src, dst, nrhs, s); break;
-        case 8: launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s); break;
+        case 1: launch_c_t<R, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 2: launch_c_t<R, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 4: launch_c_t<R, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 8: launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
         default:
-            if constexpr (sizeof(R) == 4) launch_c_t<R, 16, CJ>(ds, src, dst, nrhs, s);
-            else launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s);
+            if constexpr (sizeof(R) == 4) launch_c_t<R, 16, CJ>(ds, src, dst, nrhs, s, persist);
+            else launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist);
     }
 }
 
 template <class R>
-void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s) {
+void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
+              bool persist = false) {
     if (ds.n_items_c == 0) return;
-    if (nrhs == 1) {
+    if (nrhs == 1 && (force == 0 || force == MIDBF_CHOICE_COLUMN1)) {
         const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
         if (sm <= kSmemCap) {
             if (conj) {
                 auto kf = k_pattern_c1<R, true>;
                 set_smem(kf, sm);
-                kf<<<ds.n_items_c1, kThreads, sm, s>>>(ds.ids1, src, dst);
+                kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, ds.n_items_c1, persist), kThreads, sm, s>>>(ds.ids1, src, dst, ds.n_items_c1);
             } else {
                 auto kf = k_pattern_c1<R, false>;
                 set_smem(kf, sm);
-                kf<<<ds.n_items_c1, kThreads, sm, s>>>(ds.ids1, src, dst);
+                kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, ds.n_items_c1, persist), kThreads, sm, s>>>(ds.ids1, src, dst, ds.n_items_c1);
             }
             CK(cudaGetLastError());
             return;
         }
     }
-    const int nr = pick_nr<R>(nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
-    if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s);
-    else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s);
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
+    if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
+    else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
     CK(cudaGetLastError());
 }
 
 template <class R, int RT, int NR, bool CJ, int PQ>
-void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s) {
+void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
     SStage<R> st = ds.ss;
     const size_t sm = s_fly_smem<R>(st.P, st.Q, RT, NR);
     auto kf = k_s_fly<R, RT, NR, CJ, PQ>;
@@ -686,10 +726,14 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
     const bool four = RT == 4;
     if (!CJ) {
         st.items = four ? ds.items_rows4 : ds.items_rows;
-        kf<<<four ? ds.n_items_rows4 : ds.n_items_rows, kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src, dst, nrhs);
+        const int n = four ? ds.n_items_rows4 : ds.n_items_rows;
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src,
+                                                                                          dst, nrhs, n);
     } else {
         st.items = four ? ds.items_cols4 : ds.items_cols;
-        kf<<<four ? ds.n_items_cols4 : ds.n_items_cols, kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src, dst, nrhs);
+        const int n = four ? ds.n_items_cols4 : ds.n_items_cols;
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src,
+                                                                                          dst, nrhs, n);
     }
 }
 
@@ -697,42 +741,43 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
 // time for the workload families.  FP64: the general shape (the plain form
 // stores the middle factor by default).
 template <class R, bool CJ, int PQ>
-void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     if constexpr (sizeof(R) == 4) {
         switch (nr) {
-            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s); break;
-            case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s); break;
-            case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s); break;
-            case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s); break;
-            default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s);
+            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s, persist);
         }
     } else {
         switch (nr) {
-            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s); break;
-            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s); break;
-            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s); break;
-            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s);
+            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s, persist);
         }
     }
 }
 
 template <class R, bool CJ>
-void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s) {
+void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     switch (sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0) {
-        case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s); break;
-        case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s); break;
-        case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s); break;
-        case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s); break;
-        case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s); break;
-        default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s);
+        case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s, persist); break;
+        default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s, persist);
     }
 }
 
 template <class R>
-void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s) {
-    const int nr = pick_nr<R>(nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
-    if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s);
-    else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s);
+void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s, int force = 0,
+              bool persist = false) {
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
+    if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
+    else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
     CK(cudaGetLastError());
 }
 
@@ -783,7 +828,7 @@ void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, 
 template <bool RF>
 void launch_blk_tc_t(const TcStage& st, int items, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
                      cudaStream_t s) {
-    const size_t sm = tcb_smem_bytes<RF>();
+    const size_t sm = tc_smem_bytes<RF>();
     auto kf = k_blk_tc<RF>;
     set_smem(kf, sm);
     kf<<<items, kTcThreads, sm, s>>>(st, src, dst, nrhs, status);
@@ -804,6 +849,55 @@ int count_launches(const std::vector<DevStage<R>>& st) {
     for (auto& s : st) n += 1;
     return n;
 }
+
+// SIMT RHS tile named by a choice (0: none).
+inline int choice_tile(int choice) {
+    const int base = choice == MIDBF_CHOICE_TENSOR ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
+    return base >= 1 && base <= 16 ? base : 0;
+}
+
+inline bool valid_choice(int choice) {
+    if (choice == MIDBF_CHOICE_TENSOR) return true;
+    const int base = choice & ~MIDBF_CHOICE_PERSIST;
+    return base == MIDBF_CHOICE_DEFAULT || base == MIDBF_CHOICE_COLUMN1 || base == 1 || base == 2 || base == 4 ||
+           base == 8 || base == 16;
+}
+
+// One stage launch.  choice: MIDBF_CHOICE_DEFAULT (the built-in rules: tensor
+// cores in the BF16 modes from kTcMinRhs / kTcBlkMinRhs RHS on, else the SIMT
+// kernel with the RHS tile of pick_nr), a SIMT RHS tile (1, 2, 4, 8, 16) or
+// MIDBF_CHOICE_COLUMN1 (the one-RHS pattern-C kernel), optionally with
+// MIDBF_CHOICE_PERSIST, or MIDBF_CHOICE_TENSOR.
+template <class R>
+void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, VecRef<R> src, VecRef<R> dst, int nrhs,
+                  int choice, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        const bool tc_ok = ds.id ? ds.tc : dp->tc_mode != 0;
+        const bool use_tc = tc_ok && (choice == MIDBF_CHOICE_TENSOR ||
+                                      (choice == MIDBF_CHOICE_DEFAULT && nrhs >= (ds.id ? kTcBlkMinRhs : kTcMinRhs)));
+        if (use_tc) {
+            if (ds.id) launch_blk_tc(ds, adjoint ? 1 : 0, src, dst, nrhs, dp->tc_mode == 2, dp->d_status, s);
+            else launch_tc(ds, src, dst, nrhs, adjoint, dp->tc_mode == 2, dp->d_status, s);
+            return;
+        }
+    }
+    const bool persist = choice != MIDBF_CHOICE_TENSOR && (choice & MIDBF_CHOICE_PERSIST) != 0;
+    const int tile = choice_tile(choice);
+    const bool col1 = choice != MIDBF_CHOICE_TENSOR && (choice & ~MIDBF_CHOICE_PERSIST) == MIDBF_CHOICE_COLUMN1;
+    if (ds.id) {
+        const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
+        // pattern R computes narrow from wide; pattern C wide from narrow.
+        const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
+        if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
+        else launch_c<R>(ds, src, dst, nrhs, adjoint, s, col1 ? MIDBF_CHOICE_COLUMN1 : tile, persist);
+    } else {
+        launch_s<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
+    }
+}
+
+// Choice recorded by the autotuner (or midbf_set_choice) for this RHS count,
+// stage and direction; MIDBF_CHOICE_DEFAULT when there is none.
+int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint);
 
 // Run all stages.  user_in/user_out: caller vectors (column-major with ld).
 template <class R>
@@ -835,26 +929,7 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
         VecRef<R> fout = ds.out_user ? (adjoint ? uin : uout) : internal(sidx);
         VecRef<R> src = adjoint ? fout : fin;
         VecRef<R> dst = adjoint ? fin : fout;
-        bool tc_done = false;
-        if constexpr (sizeof(R) == 4) {
-            if (ds.id && ds.tc && nrhs >= kTcBlkMinRhs) {
-                launch_blk_tc(ds, adjoint ? 1 : 0, src, dst, nrhs, dp->tc_mode == 2, dp->d_status, s);
-                tc_done = true;
-            }
-        }
-        if (tc_done) {
-        } else if (ds.id) {
-            const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
-            // pattern R computes narrow from wide; pattern C wide from narrow.
-            const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
-            if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s);
-            else launch_c<R>(ds, src, dst, nrhs, adjoint, s);
-        } else if constexpr (sizeof(R) == 4) {
-            if (dp->tc_mode && nrhs >= kTcMinRhs) launch_tc(ds, src, dst, nrhs, adjoint, dp->tc_mode == 2, dp->d_status, s);
-            else launch_s<R>(ds, src, dst, nrhs, adjoint, s);
-        } else {
-            launch_s<R>(ds, src, dst, nrhs, adjoint, s);
-        }
+        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, tuned_choice(dp, nrhs, sidx, adjoint), s);
         if (dp->profile) CK(cudaEventRecord(dp->ev[2 * q + 1], s));
     }
 }
@@ -1039,20 +1114,22 @@ void run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, c
             VecRef<R> fout = ds.out_user ? (adj ? uin : uout) : internal(sidx);
             Entry e{i, sidx, adj ? fout : fin, adj ? fin : fout};
             std::array<int, 4> key{};
+            // a tuned SIMT tile for this instance's RHS count, if any
+            const int force = choice_tile(tuned_choice(dps[i], nr, sidx, adj));
             if (ds.id) {
                 const bool wide_is_fwd_input = ds.kind != KIND_U;
                 const bool use_r = adj ? !wide_is_fwd_input : wide_is_fwd_input;
                 if (use_r) {
-                    const int t = pick_nr<R>(nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
+                    const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
                     key = {BT_R, ds.rt, t, 0};
-                } else if (nr == 1 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
+                } else if (nr == 1 && force == 0 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
                     key = {BT_C1, 0, 1, 0};
                 } else {
-                    const int t = pick_nr<R>(nr, [&](int qq) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, qq); });
+                    const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, qq); });
                     key = {BT_C, 0, t, 0};
                 }
             } else {
-                const int t = pick_nr<R>(nr, [&](int qq) {
+                const int t = forced_or_pick<R>(force, nr, [&](int qq) {
                     return s_fly_smem<R>(ds.ss.P, ds.ss.Q, qq <= 4 && sizeof(R) == 4 ? 4 : 2, qq);
                 });
                 const int rt = (t <= 4 && sizeof(R) == 4) ? 4 : 2;
@@ -1072,11 +1149,212 @@ void run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, c
     }
 }
 
+int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint) {
+    if (dp->tuned.empty()) return MIDBF_CHOICE_DEFAULT;
+    auto it = dp->tuned.find(nrhs);
+    if (it == dp->tuned.end() || sidx >= (int)it->second.size()) return MIDBF_CHOICE_DEFAULT;
+    return it->second[sidx][adjoint ? 1 : 0];
+}
+
+// Kernel variants worth timing for a stage and direction.
+template <class R>
+std::vector<int> stage_candidates(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, int nrhs) {
+    std::vector<int> c;
+    const int cap = sizeof(R) == 4 ? 16 : 8;
+    int top = 1;
+    while (top < nrhs && top < cap) top *= 2;
+    bool use_r = false;
+    if (ds.id) {
+        const bool wide_is_fwd_input = ds.kind != KIND_U;
+        use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
+    }
+    for (int nr = 1; nr <= top; nr *= 2) {
+        size_t sm = 0;
+        if (ds.id) sm = use_r ? pattern_r_smem<R>(ds.max_nred, ds.rt, nr) : pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, nr);
+        else sm = s_fly_smem<R>(ds.ss.P, ds.ss.Q, nr <= 4 && sizeof(R) == 4 ? 4 : 2, nr);
+        if (sm <= kSmemCap) {
+            c.push_back(nr);
+            c.push_back(nr | MIDBF_CHOICE_PERSIST);
+        }
+    }
+    if (ds.id && !use_r && nrhs == 1 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
+        c.push_back(MIDBF_CHOICE_COLUMN1);
+        c.push_back(MIDBF_CHOICE_COLUMN1 | MIDBF_CHOICE_PERSIST);
+    }
+    if (sizeof(R) == 4 && (ds.id ? ds.tc : dp->tc_mode != 0)) c.push_back(MIDBF_CHOICE_TENSOR);
+    return c;
+}
+
+// Time every candidate of every stage in both directions on zero vectors of
+// the plan's sizes (the kernels' cost does not depend on the values) and keep
+// the fastest: one untimed launch, then the minimum of three timed ones.
+template <class R>
+void autotune(midbf_dplan* dp, const std::vector<DevStage<R>>& stages, int nrhs, cudaStream_t s) {
+    const size_t ce = sizeof(cx<R>);
+    const int64_t nuser = std::max(dp->nx, dp->nw);
+    const size_t ub = (size_t)nuser * nrhs * ce, ib = (size_t)std::max<int64_t>(dp->max_space, 1) * nrhs * ce;
+    void* mem = nullptr;
+    if (cudaMalloc(&mem, 2 * ub + 2 * ib) != cudaSuccess) fail(MIDBF_ENOMEM, "autotune: cudaMalloc of the trial vectors failed");
+    struct Free {
+        void* p;
+        ~Free() { cudaFree(p); }
+    } guard{mem};
+    CK(cudaMemsetAsync(mem, 0, 2 * ub + 2 * ib, s));
+    cx<R>* ubuf[2] = {static_cast<cx<R>*>(mem), reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + ub)};
+    cx<R>* ibuf[2] = {reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + 2 * ub),
+                      reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + 2 * ub + ib)};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int ns = (int)stages.size();
+    std::vector<std::array<int, 2>> best(ns, {MIDBF_CHOICE_DEFAULT, MIDBF_CHOICE_DEFAULT});
+    try {
+        for (int sidx = 0; sidx < ns; ++sidx) {
+            const DevStage<R>& ds = stages[sidx];
+            for (int a = 0; a < 2; ++a) {
+                const bool adjoint = a == 1;
+                // the same vector roles as run(): user vectors at the ends, internal spaces between
+                VecRef<R> fin = sidx == 0 ? VecRef<R>{ubuf[0], 1, nuser} : VecRef<R>{ibuf[(sidx - 1) & 1], nrhs, 1};
+                VecRef<R> fout = ds.out_user ? VecRef<R>{ubuf[1], 1, nuser} : VecRef<R>{ibuf[sidx & 1], nrhs, 1};
+                VecRef<R> src = adjoint ? fout : fin, dst = adjoint ? fin : fout;
+                float best_ms = 1e30f;
+                for (int cand : stage_candidates<R>(dp, ds, adjoint, nrhs)) {
+                    launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, s);
+                    float t = 1e30f;
+                    for (int rep = 0; rep < 3; ++rep) {
+                        CK(cudaEventRecord(e0, s));
+                        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, s);
+                        CK(cudaEventRecord(e1, s));
+                        CK(cudaEventSynchronize(e1));
+                        float ms = 0.f;
+                        CK(cudaEventElapsedTime(&ms, e0, e1));
+                        t = std::min(t, ms);
+                    }
+                    if (t < best_ms) {
+                        best_ms = t;
+                        best[sidx][a] = cand;
+                    }
+                }
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    dp->tuned[nrhs] = best;
+}
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &st));
+    return st != cudaStreamCaptureStatusNone;
+}
+
 }  // namespace
+
+// A recorded sequence of apply calls (midbf_capture_begin / _end).
+struct midbf_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~midbf_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // C ABI
 extern "C" {
+
+int midbf_autotune(midbf_dplan* dp, int nrhs, void* stream) {
+    try {
+        if (!dp || nrhs <= 0) fail(MIDBF_EINVAL, "bad argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (capturing(s)) fail(MIDBF_EINVAL, "midbf_autotune cannot run while the stream records a graph");
+        if (dp->precision == MIDBF_FP32) autotune<float>(dp, dp->st32, nrhs, s);
+        else autotune<double>(dp, dp->st64, nrhs, s);
+        int st = 0;
+        CK(cudaMemcpy(&st, dp->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st != 0) fail(MIDBF_ETIMEOUT, "a tensor-core wait gave up during tuning");
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        set_last_error("host allocation failed");
+        return MIDBF_ENOMEM;
+    }
+}
+
+int midbf_set_choice(midbf_dplan* dp, int nrhs, int stage, int adjoint, int choice) {
+    if (!dp || nrhs <= 0 || stage < 0 || stage >= (int)dp->stage_kind.size()) {
+        set_last_error("midbf_set_choice: bad argument");
+        return MIDBF_EINVAL;
+    }
+    if (!valid_choice(choice)) {
+        set_last_error("midbf_set_choice: unknown choice");
+        return MIDBF_EINVAL;
+    }
+    auto& v = dp->tuned[nrhs];
+    if (v.empty()) v.assign(dp->stage_kind.size(), {MIDBF_CHOICE_DEFAULT, MIDBF_CHOICE_DEFAULT});
+    v[stage][adjoint ? 1 : 0] = choice;
+    return MIDBF_OK;
+}
+
+int midbf_get_choice(const midbf_dplan* dp, int nrhs, int stage, int adjoint, int* choice) {
+    if (!dp || !choice || nrhs <= 0 || stage < 0 || stage >= (int)dp->stage_kind.size()) {
+        set_last_error("midbf_get_choice: bad argument");
+        return MIDBF_EINVAL;
+    }
+    *choice = tuned_choice(dp, nrhs, stage, adjoint != 0);
+    return MIDBF_OK;
+}
+
+int midbf_capture_begin(void* stream) {
+    try {
+        if (!stream) fail(MIDBF_EINVAL, "the legacy default stream cannot record a graph");
+        CK(cudaStreamBeginCapture(static_cast<cudaStream_t>(stream), cudaStreamCaptureModeThreadLocal));
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+int midbf_capture_end(void* stream, midbf_graph** graph) {
+    try {
+        if (!stream || !graph) fail(MIDBF_EINVAL, "null argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (!capturing(s)) fail(MIDBF_EINVAL, "no recording in progress on this stream");
+        auto g = std::make_unique<midbf_graph>();
+        cudaError_t e = cudaStreamEndCapture(s, &g->graph);
+        if (e != cudaSuccess) fail(MIDBF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+        if (e != cudaSuccess) fail(MIDBF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+        *graph = g.release();
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+int midbf_graph_launch(const midbf_graph* graph, void* stream) {
+    try {
+        if (!graph) fail(MIDBF_EINVAL, "null graph");
+        CK(cudaGraphLaunch(graph->exec, static_cast<cudaStream_t>(stream)));
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
+void midbf_graph_destroy(midbf_graph* graph) { delete graph; }
+
 
 int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out) {
     try {
@@ -1227,6 +1505,7 @@ int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin
         if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
         if (dp->nw >= (1LL << 31) || dp->nx >= (1LL << 31)) fail(MIDBF_EINVAL, "vectors longer than 2^31");
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (dp->profile && capturing(s)) fail(MIDBF_EINVAL, "profiling is on: the apply cannot be recorded into a graph");
         if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
         else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
         return MIDBF_OK;
@@ -1302,6 +1581,7 @@ int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, vo
         char* din = base + need;
         char* dout = din + (size_t)nin * nrhs * ce;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (capturing(s)) fail(MIDBF_EINVAL, "midbf_apply_host cannot be recorded into a graph");
         CK(cudaMemcpyAsync(din, in_host, (size_t)nin * nrhs * ce, cudaMemcpyHostToDevice, s));
         int rc = midbf_apply(dp, adjoint, din, nin, dout, nout, nrhs, stream, workspace, need);
         if (rc != MIDBF_OK) return rc;

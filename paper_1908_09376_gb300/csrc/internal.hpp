@@ -45,7 +45,16 @@ struct Sub {
     int32_t m = 0;               // wide size (block input for V, output for U)
     std::vector<int32_t> skel;   // k positions in [0, m)
     std::vector<int32_t> red;    // m - k positions
-    std::vector<cplx> T;         // k x (m - k), row-major
+    std::vector<cplx> T;         // k x (m - k), row-major (FP64 storage)
+    std::vector<std::complex<float>> Tf;   // the same in FP32 (params.store_fp32); then T is empty
+    size_t t_size() const { return Tf.empty() ? T.size() : Tf.size(); }
+    cplx t(size_t i) const { return Tf.empty() ? T[i] : cplx(Tf[i].real(), Tf[i].imag()); }
+    // keep T in FP32 only
+    void to_fp32() {
+        Tf.resize(T.size());
+        for (size_t i = 0; i < T.size(); ++i) Tf[i] = std::complex<float>((float)T[i].real(), (float)T[i].imag());
+        std::vector<cplx>().swap(T);
+    }
 };
 
 struct Block {

@@ -96,7 +96,13 @@ std::vector<uint8_t> plan_serialize(const Plan& pl) {
                 w.put<int32_t>(s.m);
                 w.put_vec(s.skel);
                 w.put_vec(s.red);
-                w.put_vec(s.T);
+                if (s.Tf.empty()) {
+                    w.put_vec(s.T);
+                } else {
+                    std::vector<cplx> t64(s.Tf.size());
+                    for (size_t i = 0; i < t64.size(); ++i) t64[i] = s.t(i);
+                    w.put_vec(t64);
+                }
             }
         }
     }
@@ -211,8 +217,11 @@ void plan_validate(const Plan& pl) {
                 for (int32_t v : sb.red) {
                     if (v < 0 || v >= sb.m || seen[v]++) fail(MIDBF_EFORMAT, "bad redundant set");
                 }
-                for (const cplx& z : sb.T)
+                if (sb.t_size() != (size_t)sb.k * (size_t)(sb.m - sb.k)) fail(MIDBF_EFORMAT, "T has the wrong size");
+                for (size_t i = 0; i < sb.t_size(); ++i) {
+                    const cplx z = sb.t(i);
                     if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) fail(MIDBF_EFORMAT, "non-finite T");
+                }
                 ksum += sb.k;
             }
             if (ksum != narrow) fail(MIDBF_EFORMAT, "sub-block ranks do not add up to the narrow side");
@@ -245,7 +254,7 @@ void plan_stats(const Plan& pl, midbf_stats* st) {
             }
             for (const Sub& sb : b.subs) {
                 st->nsubs++;
-                st->t_entries += (int64_t)sb.T.size();
+                st->t_entries += (int64_t)sb.t_size();
                 st->skel_entries += sb.k;
                 st->max_rank = std::max(st->max_rank, (int)sb.k);
                 ranks += sb.k;

@@ -1,22 +1,31 @@
-// Tensor-core (tcgen05) middle factor for many right-hand sides, sm_103a.
+// Tensor-core (tcgen05) apply for many right-hand sides, sm_103a.
 //
-// For one S block (Sec. 3.5) and a tile of 128 rows, D (128 x 2R') =
-// A (128 x 2K) * B' (2K x 2R') on the 5th-generation tensor cores, where
-//   A  = the block's kernel entries exp(2 pi i Phi) generated on the fly in
-//        BF16, complex entries interleaved (re, im) along K;
-//   B' = the real embedding of the RHS block Y (K x R'):
-//        B'[2k][2n] = Re Y, B'[2k][2n+1] = Im Y, B'[2k+1][2n] = -Im Y,
-//        B'[2k+1][2n+1] = Re Y,
-// so that D[:, 2n] + i D[:, 2n+1] = (S Y)[:, n] with FP32 accumulation in
-// tensor memory.  With refinement each operand is split into BF16 hi + lo
-// (lo = bf16(v - hi)) and D accumulates A_hi B_hi + A_hi B_lo + A_lo B_hi.
+// Both kernels compute, for one block of a stage and a tile of 128 output
+// rows, the complex product Z (128 x R) = A (128 x K) Y (K x R) on the
+// 5th-generation tensor cores with FP32 accumulation in tensor memory (TMEM):
+//   * k_s_tc:   A is a middle-factor block S (Sec. 3.5) made on the fly from
+//               the split phase of its rows and columns;
+//   * k_blk_tc: A is a V or U block of interpolative decompositions
+//               (Sec. 3.2), read from dense BF16 tile images.
+// The complex product runs through a real embedding of A: with
+//   A_top = (Re A, -Im A) and A_bot = (Im A, Re A) interleaved along K, and
+//   B     = (Re Y, Im Y)  interleaved along K (row n of B = RHS n),
+// D_top = A_top B^T = Re(A Y) and D_bot = A_bot B^T = Im(A Y).  D_top sits in
+// TMEM columns [0, 256), D_bot in [256, 512), so one pass covers 256 RHS.
+// With refinement every operand is split into BF16 hi + lo (lo = bf16(v -
+// hi)) and D accumulates hi*hi + hi*lo + lo*hi (the lo*lo product is of the
+// order of the FP32 accumulation's rounding).
 //
-// Operands live in shared memory in the no-swizzle K-major core-matrix layout
-// (8 rows x 16 bytes per core matrix; leading byte offset 128 between core
-// matrices along K, stride byte offset (K/8)*128 between 8-row groups).  One
-// thread issues the MMAs; tcgen05.commit arrives on an mbarrier per pipeline
-// stage, so generating column chunk c+1 overlaps the MMAs of chunk c.  Every
-// wait is bounded; a wait that gives up sets the plan's status word.
+// Operands live in shared memory in the no-swizzle K-major core-matrix
+// layout (8 rows x 16 bytes per core matrix; byte offset 128 between core
+// matrices along K, (K/8)*128 between 8-row groups).  A CTA is 8 producer
+// warps and one MMA warp around a ring of S stages of 16 complex columns:
+// producers fill stage s and arrive on full[s]; the MMA warp's first lane
+// issues the MMAs of the stage and commits them to empty[s].  Producers
+// gather the right-hand sides of the next stage while they fill this one.  In k_blk_tc
+// the MMA warp also issues the bulk copies of the A tiles, S - 1 chunks
+// ahead.  Every wait is bounded: a wait that gives up sets the plan's status
+// word to MIDBF_ETIMEOUT and the CTA winds down without writing outputs.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -24,6 +33,37 @@
 #include "kernels.cuh"
 
 namespace midbf_dev {
+
+constexpr int kTcM = 128;                      // rows per item (TMEM lanes)
+constexpr int kTcKc = 16;                      // complex columns per ring stage
+constexpr int kTcK = 2 * kTcKc;                // K of a stage: (re, im) interleaved
+constexpr int kTcR = 256;                      // RHS per pass
+constexpr int kTcProducers = 512;              // producer threads (16 warps)
+constexpr int kTcThreads = kTcProducers + 32;  // + the MMA warp
+constexpr int kTcColStride = 12;               // reals per column of phase-split data (1 + P + Q <= 12)
+constexpr int kTcAElems = kTcM * kTcK;         // BF16 elements of one A part (8 KB)
+constexpr int kTcBElems = kTcR * kTcK;         // BF16 elements of one B part (16 KB)
+constexpr int kTcTileElems = kTcAElems;        // one image tile part: 128 rows x 16 complex columns
+
+template <bool REFINE>
+struct TcCfg {
+    static constexpr int NP = REFINE ? 2 : 1;  // BF16 parts per operand (hi, lo)
+    static constexpr int S = REFINE ? 3 : 4;   // ring stages
+    // one stage: A_top[NP], A_bot[NP], B[NP]
+    static constexpr size_t stage_elems = (size_t)NP * (2 * kTcAElems + kTcBElems);
+    static constexpr size_t bar_bytes = 256;   // mbarriers, TMEM address
+    static constexpr size_t smem = (size_t)S * stage_elems * 2 + bar_bytes;
+};
+
+template <bool REFINE>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+    return TcCfg<REFINE>::smem;
+}
+
+// Offset (elements) of (row r, k) in the K-major core-matrix layout with K columns.
+__host__ __device__ __forceinline__ int core_off(int r, int k, int K) {
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -55,61 +95,292 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar)));
 }
 
-// Bounded wait for the completion of the mbarrier phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
-    uint32_t done = 0;
-    for (int it = 0; it < (1 << 24) && !done; ++it) {
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kTcWaitNs = 2000000000ull;  // 2 s: far above any wait of a working pipeline
+
+// Bounded wait for the completion of the mbarrier phase with the given
+// parity.  Gives up after kTcWaitNs, or at once when the status word shows
+// that some CTA has already given up (so one failure does not make every
+// later CTA wait out its own limit).  status = nullptr: the time limit only
+// (the drain waits before TMEM is released and the CTA exits).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, const int* status) {
+    const uint64_t t0 = global_ns();
+    for (uint32_t it = 0;; ++it) {
+        uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
-            : "r"(smem_u32(mbar)), "r"(parity));
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63) {
+            if (status && *reinterpret_cast<const volatile int*>(status) != 0) return false;
+            if (global_ns() - t0 > kTcWaitNs) return false;
+        }
     }
-    return done != 0;
 }
 
-// Offset (elements) of (row r, k) in the K-major core-matrix layout with K columns.
-__device__ __forceinline__ int core_off(int r, int k, int K) {
-    return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
-    return (uint32_t)__bfloat16_as_ushort(lo_half) | ((uint32_t)__bfloat16_as_ushort(hi_half) << 16);
+// Producer-only named barrier (barrier 1, the 8 producer warps) that returns
+// the AND of a predicate over them, so that the outcome of a bounded wait is
+// uniform before any producer acts on it.
+__device__ __forceinline__ bool producers_and(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 q, %1, 0;\n\t"
+        "bar.red.and.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kTcProducers)
+        : "memory");
+    return r != 0;
 }
 
-__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __float2bfloat16_rn(v);
-    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+// (re, im) -> packed BF16 pair (re in the low half), and the pair of the
+// remainders v - bf16(v) rounded to BF16.
+__device__ __forceinline__ void split_pair(float re, float im, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    const float rh = __uint_as_float(hi << 16), ih = __uint_as_float(hi & 0xffff0000u);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(re - rh, im - ih);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-constexpr int kTcM = 128;         // rows per item
-constexpr int kTcCols = 32;       // complex columns per pipeline chunk (K' = 64)
-constexpr int kTcK = 2 * kTcCols;
-constexpr int kTcThreads = 256;
-constexpr int kTcMaxR = 128;      // RHS per accumulator (N = 2 R' <= 256)
-constexpr int kTcColStride = 12;  // reals per column of phase-split data (1 + P + Q <= 12)
+// Packed BF16 pairs: (a, b) -> (a, -b); (a, b) -> (b, a); (a, -b) -> (b, a).
+__device__ __forceinline__ uint32_t neg_high(uint32_t w) { return w ^ 0x80000000u; }
+__device__ __forceinline__ uint32_t swap_halves(uint32_t w) { return __byte_perm(w, 0, 0x1032); }
+__device__ __forceinline__ uint32_t top_to_bot(uint32_t w) { return swap_halves(w) ^ 0x00008000u; }
+
+// Shared-memory control block after the ring.
+template <int S>
+struct TcBars {
+    uint64_t full[S];    // producers -> MMA warp (count kTcProducers)
+    uint64_t empty[S];   // MMAs of the stage complete (tcgen05.commit)
+    uint64_t aload[S];   // bulk copy of the stage's A tiles landed (k_blk_tc)
+    uint64_t done;       // all MMAs of a pass complete
+    uint64_t tfree;      // the epilogue of a pass has read TMEM (count kTcProducers)
+    uint64_t fin;        // teardown: every MMA issued has completed
+    uint32_t taddr;
+};
+
+// MMAs of one ring stage: D_top += A_top B^T and D_bot += A_bot B^T over the
+// stage's K = 32, plus the hi/lo refinement products.
+template <bool REFINE>
+__device__ __forceinline__ void tc_issue_stage(uint32_t tmem, const __nv_bfloat16* stage, uint32_t idesc,
+                                               bool first) {
+    constexpr int NP = REFINE ? 2 : 1;
+    constexpr uint32_t sbo = (kTcK / 8) * 128;
+    const uint32_t aT = smem_u32(stage);
+    const uint32_t aB = aT + NP * kTcAElems * 2;
+    const uint32_t bB = aT + 2 * NP * kTcAElems * 2;
+#pragma unroll
+    for (int kk = 0; kk < kTcK; kk += 16) {
+        const uint32_t ko = (uint32_t)(kk / 8) * 128;
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        const uint64_t bh = umma_desc(bB + ko, 128, sbo);
+        const uint64_t th = umma_desc(aT + ko, 128, sbo);
+        const uint64_t uh = umma_desc(aB + ko, 128, sbo);
+        umma_bf16(tmem, th, bh, idesc, acc);
+        umma_bf16(tmem + kTcR, uh, bh, idesc, acc);
+        if (REFINE) {
+            const uint64_t bl = umma_desc(bB + kTcBElems * 2 + ko, 128, sbo);
+            const uint64_t tl = umma_desc(aT + kTcAElems * 2 + ko, 128, sbo);
+            const uint64_t ul = umma_desc(aB + kTcAElems * 2 + ko, 128, sbo);
+            umma_bf16(tmem, th, bl, idesc, 1u);
+            umma_bf16(tmem, tl, bh, idesc, 1u);
+            umma_bf16(tmem + kTcR, uh, bl, idesc, 1u);
+            umma_bf16(tmem + kTcR, ul, bh, idesc, 1u);
+        }
+    }
+}
+
+// Right-hand sides of one ring stage: rows n < Rpad of B from the stage's 16
+// columns at positions pos[0..16) of src (zero past ncol_left or R).  Item e
+// = (n, quad jq): 4 consecutive columns of RHS n = one 16-byte core row;
+// consecutive threads take consecutive RHS.  The item coordinates depend on
+// the pass only, so they are set once per pass (TcBItems).
+constexpr int kTcBItems = (kTcR * kTcKc / 4 + kTcProducers - 1) / kTcProducers;  // items per thread
+
+struct TcBItems {
+    int n[kTcBItems], jq[kTcBItems];
+    long long roff[kTcBItems];   // (r0 + n) * rs
+    bool on[kTcBItems];          // item exists (e < Rpad * 4)
+    bool live[kTcBItems];        // RHS exists (n < R)
+};
+
+__device__ __forceinline__ void tc_b_items(TcBItems& I, VecRef<float> src, int r0, int R, int Rpad, int ptid) {
+#pragma unroll
+    for (int it = 0; it < kTcBItems; ++it) {
+        const int e = ptid + it * kTcProducers;
+        I.on[it] = e < Rpad * 4;
+        I.n[it] = e % Rpad;
+        I.jq[it] = e / Rpad;
+        I.live[it] = I.on[it] && I.n[it] < R;
+        I.roff[it] = (long long)(r0 + I.n[it]) * src.rs;
+    }
+}
+
+struct TcBLoad {
+    float2 y[kTcBItems][4];
+};
+
+__device__ __forceinline__ void tc_load_b(TcBLoad& L, const TcBItems& I, const int* pos, int ncol_left,
+                                          VecRef<float> src) {
+#pragma unroll
+    for (int it = 0; it < kTcBItems; ++it) {
+        const int4 p4 = *reinterpret_cast<const int4*>(pos + 4 * (I.jq[it] & 3));
+        const int pp[4] = {p4.x, p4.y, p4.z, p4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float2 v = make_float2(0.f, 0.f);
+            if (I.live[it] && I.jq[it] * 4 + u < ncol_left) {
+                const cx<float> y = src.ptr[(long long)pp[u] * src.ps + I.roff[it]];
+                v = make_float2(y.x, y.y);
+            }
+            L.y[it][u] = v;
+        }
+    }
+}
 
 template <bool REFINE>
-__host__ __device__ constexpr size_t tc_smem_bytes() {
-    // per stage: A (128 x 64) and B' (256 x 64) BF16, doubled for hi/lo
-    return (size_t)2 * (REFINE ? 2 : 1) * ((size_t)kTcM * kTcK + (size_t)2 * kTcMaxR * kTcK) * 2 + 256;
+__device__ __forceinline__ void tc_store_b(const TcBLoad& L, const TcBItems& I, __nv_bfloat16* B) {
+#pragma unroll
+    for (int it = 0; it < kTcBItems; ++it) {
+        if (I.on[it]) {
+            uint32_t h[4], l[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) split_pair(L.y[it][u].x, L.y[it][u].y, h[u], l[u]);
+            const int o = core_off(I.n[it], 8 * I.jq[it], kTcK);
+            *reinterpret_cast<uint4*>(B + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            if (REFINE) *reinterpret_cast<uint4*>(B + kTcBElems + o) = make_uint4(l[0], l[1], l[2], l[3]);
+        }
+    }
 }
 
-// One CTA per item (block, 128 role-rows).  role rows/cols as in k_s_fly.
+// Epilogue of a pass: producer warp w reads TMEM lanes 32 (w & 3) + lane
+// (its row), column groups of 8 RHS round robin over the four warps of a lane
+// quarter; Re from D_top, Im from D_bot.
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, int Rpad, int R, int r0, bool rowok,
+                                            int op, VecRef<float> dst, bool zero) {
+    constexpr int kQuarterWarps = kTcProducers / 32 / 4;
+    const int q = warp & 3;
+    for (int c0 = 8 * (warp >> 2); c0 < Rpad; c0 += 8 * kQuarterWarps) {
+        uint32_t v[8], w[8];
+        const uint32_t a = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                     : "r"(a));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                     : "r"(a + kTcR));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (rowok) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int n = c0 + t;
+                if (n < R) {
+                    const float re = zero ? 0.f : __uint_as_float(v[t]);
+                    const float im = zero ? 0.f : __uint_as_float(w[t]);
+                    dst.ptr[(long long)op * dst.ps + (long long)(r0 + n) * dst.rs] = cx<float>{re, im};
+                }
+            }
+        }
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void tc_setup(TcBars<S>* bars, int tid, int warp) {
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bars->full[s], kTcProducers);
+            mbar_init(&bars->empty[s], 1);
+            mbar_init(&bars->aload[s], 1);
+        }
+        mbar_init(&bars->done, 1);
+        mbar_init(&bars->tfree, kTcProducers);
+        mbar_init(&bars->fin, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->taddr)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+}
+
+template <int S>
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, int warp) {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+// The MMA warp's last step: a commit that arrives once every MMA it issued
+// has completed, awaited (bounded) before the tensor memory is released.
+__device__ __forceinline__ void tc_mma_drain(uint64_t* fin, int lane, int* status) {
+    if (lane == 0) {
+        umma_commit(fin);
+        if (!mbar_wait(fin, 0, nullptr)) atomicExch(status, MIDBF_ETIMEOUT);
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Middle factor.  One CTA per item (block, 128 role-rows); role rows/cols as
+// in k_s_fly (row_is_row = 1 forward, 0 adjoint with CONJ).
+//
+// Producer iteration for chunk c (ring slot s = g mod S):
+//   wait until the stage's MMAs of chunk g - S are done; threads < 16 stage
+//   the phase data and positions of chunk c + 1 in slot (g + 1) mod S; a
+//   producer barrier; gather the RHS of chunk c + 1 into registers; generate
+//   A_top / A_bot of chunk c; store the RHS of chunk c (gathered one
+//   iteration earlier) as B; arrive on full[s].
+// A slot is rewritten S - 1 iterations after it was last read; S >= 3 and the
+// barrier of every iteration keep that ordered.
 template <int PQ, bool REFINE, bool CONJ>
 __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<float> rs, SSide<float> cs,
                                                         VecRef<float> src, VecRef<float> dst, int nrhs,
                                                         int row_is_row, int* status) {
-    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    using Cfg = TcCfg<REFINE>;
+    constexpr int S = Cfg::S, NP = Cfg::NP;
+    static_assert(S >= 3, "slot reuse needs three ring stages");
     using Sh = PhaseShape<PQ>;
-    constexpr int NP = REFINE ? 2 : 1;
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);                 // [stage][part][128*64]
-    __nv_bfloat16* sB = sA + 2 * NP * kTcM * kTcK;                                    // [stage][part][256*64]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 2 * NP * 2 * kTcMaxR * kTcK);  // [2]
-    uint32_t* taddr = reinterpret_cast<uint32_t*>(mbar + 2);
-    __shared__ float scol[kTcCols * kTcColStride];
-    __shared__ int spos[kTcCols];
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);
+    TcBars<S>* bars = reinterpret_cast<TcBars<S>*>(tc_smem_raw + S * Cfg::stage_elems * 2);
+    __shared__ float scol[S][kTcKc * kTcColStride];
+    __shared__ __align__(16) int spos[S][kTcKc];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 it = st.items[blockIdx.x];
     const int b = it.x;
@@ -119,238 +390,171 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
     const int ncol = row_is_row ? st.blk_ncol[b] : st.blk_nrow[b];
     const int P = Sh::fixed ? Sh::P : st.P;
     const int Q = Sh::fixed ? Sh::Q : st.Q;
+    const int nchunk = (ncol + kTcKc - 1) / kTcKc;
+    const int npass = (nrhs + kTcR - 1) / kTcR;
 
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr)),
-                     "r"(256));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = *taddr;
+    tc_setup<S>(bars, tid, warp);
+    const uint32_t tmem = bars->taddr;
 
-    // this thread's row of the item (two threads per row, 16 columns each)
-    const int row = tid & (kTcM - 1), half = tid >> 7;
-    const int i = it.y + row;
-    const bool rok = i < nrow;
-    float ra = 0.f, ru[Sh::P], rc[Sh::Q > 0 ? Sh::Q : 1];
-    {
-        const int ii = rok ? i : 0;
-        ra = rs.a[ro + ii];
-#pragma unroll
-        for (int p = 0; p < Sh::P; ++p) ru[p] = p < P ? rs.u[(size_t)(ro + ii) * P + p] : 0.f;
-#pragma unroll
-        for (int q = 0; q < Sh::Q; ++q) rc[q] = q < Q ? rs.c[(size_t)(ro + ii) * Q + q] : 0.f;
-    }
-    uint32_t commits[2] = {0, 0};   // commits issued per stage
-    bool pending[2] = {false, false};  // latest commit of the stage not yet waited for
-    bool ok = true;
-    const int nchunk = (ncol + kTcCols - 1) / kTcCols;
-    for (int r0 = 0; r0 < nrhs && ok; r0 += kTcMaxR) {
-        const int nr = min(kTcMaxR, nrhs - r0);
-        const int N = ((2 * nr + 15) / 16) * 16;
-        const uint32_t idesc = umma_idesc_bf16(kTcM, N);
-        for (int c = 0; c < nchunk && ok; ++c) {
-            const int s = c & 1;
-            // the stage's previous MMAs (chunk c-2) must be done before overwriting it;
-            // the outcome of the bounded wait is made block-uniform before acting on it
-            if (pending[s]) {
-                const bool w = mbar_wait(&mbar[s], (commits[s] - 1) & 1);
-                ok = __syncthreads_and(w) != 0;
-                if (!ok) break;
-                pending[s] = false;
+    if (warp == kTcProducers / 32) {
+        // ---- MMA warp
+        bool ok = true;
+        int g = 0;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int R = min(kTcR, nrhs - p * kTcR), Rpad = (R + 15) & ~15;
+            const uint32_t idesc = umma_idesc_bf16(kTcM, Rpad);
+            if (p > 0 && !mbar_wait(&bars->tfree, (uint32_t)(p - 1) & 1, status)) {
+                ok = false;
+                break;
             }
-            // this chunk's column data (phase split, positions) into shared memory
-            {
-                const int jb = c * kTcCols;
-                if (tid < kTcCols) {
-                    const int j = jb + tid;
-                    float* cj = scol + tid * kTcColStride;
-                    if (j < ncol) {
-                        const int e = co + j;
-                        cj[0] = cs.a[e];
-                        for (int p = 0; p < P; ++p) cj[1 + p] = cs.u[(size_t)e * P + p];
-                        for (int q = 0; q < Q; ++q) cj[1 + P + q] = cs.c[(size_t)e * Q + q];
-                        spos[tid] = cs.pos[e];
-                    } else {
-                        spos[tid] = 0;
-                    }
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int s = g % S;
+                if (!mbar_wait(&bars->full[s], (uint32_t)(g / S) & 1, status)) {
+                    ok = false;
+                    break;
                 }
-                __syncthreads();
-            }
-            __nv_bfloat16* A0 = sA + (size_t)(s * NP) * kTcM * kTcK;
-            __nv_bfloat16* B0 = sB + (size_t)(s * NP) * 2 * kTcMaxR * kTcK;
-            const int j0 = c * kTcCols;
-            // A: this thread's row, 16 complex columns = 4 core-matrix rows of
-            // 8 BF16 (4 complex entries) each, stored as 16-byte vectors
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                uint32_t hv[4], lv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int jj = half * 16 + q4 * 4 + u;
-                    const int j = j0 + jj;
-                    float er = 0.f, ei = 0.f;
-                    if (rok && j < ncol) {
-                        const float* cj = scol + jj * kTcColStride;
-                        float th = ra + cj[0];
-#pragma unroll
-                        for (int p = 0; p < Sh::P; ++p)
-                            if (Sh::fixed || p < P) th = fmaf(ru[p], cj[1 + p], th);
-                        if (Sh::Q > 0 && (Sh::fixed || Q > 0)) {
-                            float sq = 0.f;
-#pragma unroll
-                            for (int q = 0; q < Sh::Q; ++q)
-                                if (Sh::fixed || q < Q) sq = fmaf(rc[q], cj[1 + P + q], sq);
-                            th += sqrtf(sq);
-                        }
-                        th -= rintf(th);
-                        sincos2pi(th, &ei, &er);
-                        if (CONJ) ei = -ei;
-                    }
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    split_bf16(er, h0, l0);
-                    split_bf16(ei, h1, l1);
-                    hv[u] = pack_bf16(h0, h1);
-                    lv[u] = pack_bf16(l0, l1);
-                }
-                const int off = core_off(row, 2 * (half * 16 + q4 * 4), kTcK);
-                *reinterpret_cast<uint4*>(A0 + off) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
-                if (REFINE) *reinterpret_cast<uint4*>(A0 + kTcM * kTcK + off) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
-            }
-            // B': for RHS n and 4 consecutive columns, rows 2n and 2n+1 of the
-            // embedding are each one 16-byte core-matrix row
-            for (int e = tid; e < (N / 2) * (kTcCols / 4); e += kTcThreads) {
-                const int jq = e / (N / 2), n = e % (N / 2);   // consecutive threads: consecutive RHS
-                uint32_t h0[4], h1[4], l0[4], l1[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int jj = jq * 4 + u;
-                    const int j = j0 + jj;
-                    float yr = 0.f, yi = 0.f;
-                    if (n < nr && j < ncol) {
-                        const cx<float> y = src.ptr[spos[jj] * src.ps + (r0 + n) * src.rs];
-                        yr = y.x;
-                        yi = y.y;
-                    }
-                    __nv_bfloat16 rh, rl, ih, il;
-                    split_bf16(yr, rh, rl);
-                    split_bf16(yi, ih, il);
-                    h0[u] = pack_bf16(rh, __hneg(ih));   // row 2n:   ( Re, -Im )
-                    h1[u] = pack_bf16(ih, rh);           // row 2n+1: ( Im,  Re )
-                    l0[u] = pack_bf16(rl, __hneg(il));
-                    l1[u] = pack_bf16(il, rl);
-                }
-                const int o0 = core_off(2 * n, 8 * jq, kTcK), o1 = core_off(2 * n + 1, 8 * jq, kTcK);
-                *reinterpret_cast<uint4*>(B0 + o0) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
-                *reinterpret_cast<uint4*>(B0 + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
-                if (REFINE) {
-                    *reinterpret_cast<uint4*>(B0 + 2 * kTcMaxR * kTcK + o0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
-                    *reinterpret_cast<uint4*>(B0 + 2 * kTcMaxR * kTcK + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncthreads();
-            if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sbo_a = (kTcK / 8) * 128, sbo_b = (kTcK / 8) * 128;
-                for (int kk = 0; kk < kTcK; kk += 16) {
-                    const uint32_t koff = (uint32_t)(kk / 8) * 128;
-                    const uint64_t ah = umma_desc(smem_u32(A0) + koff, 128, sbo_a);
-                    const uint64_t bh = umma_desc(smem_u32(B0) + koff, 128, sbo_b);
-                    const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-                    umma_bf16(tmem, ah, bh, idesc, acc0);
-                    if (REFINE) {
-                        const uint64_t al = umma_desc(smem_u32(A0 + kTcM * kTcK) + koff, 128, sbo_a);
-                        const uint64_t bl = umma_desc(smem_u32(B0 + 2 * kTcMaxR * kTcK) + koff, 128, sbo_b);
-                        umma_bf16(tmem, ah, bl, idesc, 1u);
-                        umma_bf16(tmem, al, bh, idesc, 1u);
-                    }
+                if (lane == 0) {
+                    tc_issue_stage<REFINE>(tmem, ring + (size_t)s * Cfg::stage_elems, idesc, c == 0);
+                    umma_commit(&bars->empty[s]);
                 }
-                umma_commit(&mbar[s]);
+                __syncwarp();
             }
-            commits[s]++;
-            pending[s] = true;
+            if (!ok) break;
+            if (lane == 0) umma_commit(&bars->done);
+            __syncwarp();
         }
-        if (!ok) break;
-        // wait for the outstanding commits, the older stage first
+        if (!ok && lane == 0) atomicExch(status, MIDBF_ETIMEOUT);
+        tc_mma_drain(&bars->fin, lane, status);
+    } else {
+        // ---- producers: thread = (row, quarter of the stage's 16 columns)
+        const int ptid = tid;
+        const int row = ptid & (kTcM - 1), cq = ptid >> 7;
+        const int i = it.y + row;
+        const bool rok = i < nrow;
+        float ra = 0.f, ru[Sh::P], rc[Sh::Q > 0 ? Sh::Q : 1];
         {
-            const int last = (nchunk - 1) & 1;
-            const int order[2] = {last ^ 1, last};
-            for (int q = 0; q < 2 && ok; ++q) {
-                const int sw = order[q];
-                if (pending[sw]) {
-                    const bool w = mbar_wait(&mbar[sw], (commits[sw] - 1) & 1);
-                    ok = __syncthreads_and(w) != 0;
-                    if (ok) pending[sw] = false;
-                }
-            }
-        }
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // epilogue: warps 0-3 columns [0, N/2), warps 4-7 columns [N/2, N), lanes = rows
-        {
-            const int wq = warp & 3;
-            const int rr = wq * 32 + lane;
-            const int ii = it.y + rr;
-            const int cbeg = (warp >> 2) * (N / 2), cend = cbeg + N / 2;
-            for (int c0 = cbeg; c0 < cend; c0 += 8) {
-                uint32_t v[8];
-                const uint32_t addr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7])
-                             : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (ii < nrow) {
-                    const int op = rs.pos[ro + ii];
+            const int ii = rok ? i : 0;
+            ra = rs.a[ro + ii];
 #pragma unroll
-                    for (int q = 0; q < 8; q += 2) {
-                        const int n = (c0 + q) >> 1;
-                        if (n < nr) dst.ptr[op * dst.ps + (r0 + n) * dst.rs] = cx<float>{__uint_as_float(v[q]), __uint_as_float(v[q + 1])};
-                    }
+            for (int p = 0; p < Sh::P; ++p) ru[p] = p < P ? rs.u[(size_t)(ro + ii) * P + p] : 0.f;
+#pragma unroll
+            for (int q = 0; q < Sh::Q; ++q) rc[q] = q < Q ? rs.c[(size_t)(ro + ii) * Q + q] : 0.f;
+        }
+        const int op = rok ? rs.pos[ro + i] : 0;
+        // phase data and positions of chunk c into ring slot `slot` (threads < 16)
+        auto stage_cols = [&](int c, int slot) {
+            if (ptid < kTcKc) {
+                const int j = c * kTcKc + ptid;
+                float* cj = scol[slot] + ptid * kTcColStride;
+                if (j < ncol) {
+                    const int e = co + j;
+                    cj[0] = cs.a[e];
+                    for (int q = 0; q < P; ++q) cj[1 + q] = cs.u[(size_t)e * P + q];
+                    for (int q = 0; q < Q; ++q) cj[1 + P + q] = cs.c[(size_t)e * Q + q];
+                    spos[slot][ptid] = cs.pos[e];
+                } else {
+                    spos[slot][ptid] = 0;
                 }
             }
+        };
+        bool ok = true;
+        int g = 0;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int r0 = p * kTcR;
+            const int R = min(kTcR, nrhs - r0), Rpad = (R + 15) & ~15;
+            TcBItems I;
+            tc_b_items(I, src, r0, R, Rpad, ptid);
+            TcBLoad Lcur, Lnext;
+            if (nchunk > 0) {
+                stage_cols(0, g % S);
+                producers_and(true);
+                tc_load_b(Lcur, I, spos[g % S], ncol, src);
+            }
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int s = g % S, s1 = (g + 1) % S;
+                const uint32_t u = (uint32_t)(g / S);
+                // the stage's previous MMAs (chunk g - S) must be done before it is overwritten
+                bool w = true;
+                if (u > 0) w = mbar_wait(&bars->empty[s], (u - 1) & 1, status);
+                const bool more = c + 1 < nchunk;
+                if (more) stage_cols(c + 1, s1);
+                ok = producers_and(w);
+                if (!ok) break;
+                if (more) tc_load_b(Lnext, I, spos[s1], ncol - (c + 1) * kTcKc, src);
+                __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
+                const int j0 = c * kTcKc;
+                // A: this thread's row, columns 4 cq .. 4 cq + 3 = one core row of A_top and of A_bot
+                {
+                    uint32_t th[4], tl[4], bh[4], bl[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        const int jj = cq * 4 + v;
+                        float er = 0.f, ei = 0.f;
+                        if (rok && j0 + jj < ncol) {
+                            const float* cj = scol[s] + jj * kTcColStride;
+                            float thp = ra + cj[0];
+#pragma unroll
+                            for (int q = 0; q < Sh::P; ++q)
+                                if (Sh::fixed || q < P) thp = fmaf(ru[q], cj[1 + q], thp);
+                            if (Sh::Q > 0 && (Sh::fixed || Q > 0)) {
+                                float sq = 0.f;
+#pragma unroll
+                                for (int q = 0; q < Sh::Q; ++q)
+                                    if (Sh::fixed || q < Q) sq = fmaf(rc[q], cj[1 + P + q], sq);
+                                thp += sqrtf(sq);
+                            }
+                            thp -= rintf(thp);
+                            sincos2pi(thp, &ei, &er);
+                            if (CONJ) ei = -ei;
+                        }
+                        uint32_t h, l;
+                        split_pair(er, ei, h, l);
+                        th[v] = neg_high(h);
+                        tl[v] = neg_high(l);
+                        bh[v] = swap_halves(h);
+                        bl[v] = swap_halves(l);
+                    }
+                    const int o = core_off(row, 8 * cq, kTcK);
+                    *reinterpret_cast<uint4*>(stg + o) = make_uint4(th[0], th[1], th[2], th[3]);
+                    *reinterpret_cast<uint4*>(stg + NP * kTcAElems + o) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+                    if (REFINE) {
+                        *reinterpret_cast<uint4*>(stg + kTcAElems + o) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+                        *reinterpret_cast<uint4*>(stg + (NP + 1) * kTcAElems + o) =
+                            make_uint4(bl[0], bl[1], bl[2], bl[3]);
+                    }
+                }
+                tc_store_b<REFINE>(Lcur, I, stg + 2 * NP * kTcAElems);
+                asm volatile("fence.proxy.async.shared::cta;");
+                mbar_arrive(&bars->full[s]);
+                if (more) Lcur = Lnext;
+            }
+            if (!ok) break;
+            ok = producers_and(mbar_wait(&bars->done, (uint32_t)p & 1, status));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            tc_epilogue(tmem, warp, lane, Rpad, R, r0, rok, op, dst, nchunk == 0);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(&bars->tfree);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok && ptid == 0) atomicExch(status, MIDBF_ETIMEOUT);
     }
-    if (!ok) {
-        // report, then give the MMAs still in flight one more bounded wait
-        // before the tensor memory is released
-        if (tid == 0) atomicExch(status, MIDBF_ETIMEOUT);
-        for (int sw = 0; sw < 2; ++sw)
-            if (pending[sw]) mbar_wait(&mbar[sw], (commits[sw] - 1) & 1);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    tc_teardown<S>(tmem, warp);
 }
 
-}  // namespace midbf_dev
-
-namespace midbf_dev {
-
 // ---------------------------------------------------------------------------
-// Tensor-core block GEMM for the interpolation/transfer stages (many RHS).
+// Interpolation / transfer stages (V, U) on the tensor cores.
 //
 // In the tensor-core modes every V or U block is also stored densely (its
-// identity entries included) as pre-tiled BF16 images: tile (row tile rt,
-// column chunk c) holds rows [128 rt, 128 rt + 128) x complex columns
-// [32 c, 32 c + 32) in exactly the shared-memory core-matrix layout used by
-// the MMA (hi part, then lo part), so one cp.async.bulk moves a tile.  Two
-// orientations are stored: the block itself (forward) and its conjugate
-// transpose (adjoint).  The item is (block, row tile); the right-hand sides
-// come from the block's input positions and are embedded into B' as in k_s_tc.
+// identity entries included) as BF16 tile images: tile (row tile rt, column
+// chunk c) holds A_top = (Re, -Im) of rows [128 rt, 128 rt + 128) x complex
+// columns [16 c, 16 c + 16) in exactly the core-matrix layout of a ring stage
+// (hi part, then lo part), so one cp.async.bulk moves it; A_bot is derived
+// from it in shared memory.  Two orientations are stored: the block itself
+// (forward) and its conjugate transpose (adjoint).  The item is (block, row
+// tile); the right-hand sides come from the block's input positions.
 struct TcBlock {
-    long long img_off;   // element offset (bf16) of the first tile image
+    long long img_off;   // element offset (BF16) of the block's first tile image
     int rows, cols;      // complex rows (outputs) and columns (inputs)
     int in_off, out_off; // offsets into the position arrays
 };
@@ -363,198 +567,144 @@ struct TcStage {
     const int2* items;      // (block, row tile)
 };
 
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes) : "memory");
-}
-
-constexpr int kTcTileElems = kTcM * kTcK;   // bf16 elements per tile part (16 KB)
-
-template <bool REFINE>
-__host__ __device__ constexpr size_t tcb_smem_bytes() {
-    return (size_t)2 * (REFINE ? 2 : 1) * ((size_t)kTcM * kTcK + (size_t)2 * kTcMaxR * kTcK) * 2 + 256;
-}
-
 template <bool REFINE>
 __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, VecRef<float> src, VecRef<float> dst, int nrhs,
                                                           int* status) {
+    using Cfg = TcCfg<REFINE>;
+    constexpr int S = Cfg::S, NP = Cfg::NP;
+    static_assert(S >= 3, "slot reuse needs three ring stages");
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
-    constexpr int NP = REFINE ? 2 : 1;
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);                 // [stage][part][128*64]
-    __nv_bfloat16* sB = sA + 2 * NP * kTcM * kTcK;                                    // [stage][part][256*64]
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 2 * NP * 2 * kTcMaxR * kTcK);  // [2] MMA done
-    uint64_t* fbar = mbar + 2;                                                        // [2] A tile landed
-    uint32_t* taddr = reinterpret_cast<uint32_t*>(fbar + 2);
-    __shared__ int spos[kTcCols];
+    __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);
+    TcBars<S>* bars = reinterpret_cast<TcBars<S>*>(tc_smem_raw + S * Cfg::stage_elems * 2);
+    __shared__ __align__(16) int spos[S][kTcKc];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 it = st.items[blockIdx.x];
     const TcBlock bk = st.blocks[it.x];
     const int rt = it.y;
-    const int nchunk = (bk.cols + kTcCols - 1) / kTcCols;
-    if (tid == 0) {
-        for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[q])), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr)),
-                     "r"(256));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const uint32_t tmem = *taddr;
-    uint32_t commits[2] = {0, 0}, loads[2] = {0, 0}, issued[2] = {0, 0};
-    bool pending[2] = {false, false};
-    bool ok = true;
+    const int nchunk = (bk.cols + kTcKc - 1) / kTcKc;
+    const int npass = (nrhs + kTcR - 1) / kTcR;
+    const int total = npass * nchunk;
     const __nv_bfloat16* tile0 = st.img + bk.img_off + (size_t)rt * nchunk * NP * kTcTileElems;
-    for (int r0 = 0; r0 < nrhs && ok; r0 += kTcMaxR) {
-        const int nr = min(kTcMaxR, nrhs - r0);
-        const int N = ((2 * nr + 15) / 16) * 16;
-        const uint32_t idesc = umma_idesc_bf16(kTcM, N);
-        for (int c = 0; c < nchunk && ok; ++c) {
-            const int s = c & 1;
-            if (pending[s]) {
-                const bool w = mbar_wait(&mbar[s], (commits[s] - 1) & 1);
-                ok = __syncthreads_and(w) != 0;
-                if (!ok) break;
-                pending[s] = false;
+    constexpr uint32_t kCopyBytes = NP * kTcTileElems * 2;
+
+    tc_setup<S>(bars, tid, warp);
+    const uint32_t tmem = bars->taddr;
+
+    if (warp == kTcProducers / 32) {
+        // ---- MMA warp: bulk copies of the A tiles S - 1 chunks ahead, then the MMAs
+        bool ok = true;
+        int issued = 0;
+        auto copy = [&](int gg) {
+            const int s = gg % S;
+            if (lane == 0) {
+                mbar_expect_tx(&bars->aload[s], kCopyBytes);
+                bulk_g2s(ring + (size_t)s * Cfg::stage_elems, tile0 + (size_t)(gg % nchunk) * NP * kTcTileElems,
+                         kCopyBytes, &bars->aload[s]);
             }
-            __nv_bfloat16* A0 = sA + (size_t)(s * NP) * kTcM * kTcK;
-            __nv_bfloat16* B0 = sB + (size_t)(s * NP) * 2 * kTcMaxR * kTcK;
-            // A tile(s) by one bulk copy
-            if (tid == 0) {
-                const uint32_t bytes = (uint32_t)(NP * kTcTileElems * 2);
-                mbar_expect_tx(&fbar[s], bytes);
-                bulk_g2s(A0, tile0 + (size_t)c * NP * kTcTileElems, bytes, &fbar[s]);
+        };
+        for (; issued < total && issued < S; ++issued) copy(issued);
+        int g = 0;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int R = min(kTcR, nrhs - p * kTcR), Rpad = (R + 15) & ~15;
+            const uint32_t idesc = umma_idesc_bf16(kTcM, Rpad);
+            if (p > 0 && !mbar_wait(&bars->tfree, (uint32_t)(p - 1) & 1, status)) {
+                ok = false;
+                break;
             }
-            issued[s]++;
-            if (tid < kTcCols) {
-                const int j = c * kTcCols + tid;
-                spos[tid] = j < bk.cols ? st.in_pos[bk.in_off + j] : 0;
-            }
-            __syncthreads();
-            for (int e = tid; e < (N / 2) * (kTcCols / 4); e += kTcThreads) {
-                const int jq = e / (N / 2), n = e % (N / 2);
-                uint32_t h0[4], h1[4], l0[4], l1[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int jj = jq * 4 + u;
-                    const int j = c * kTcCols + jj;
-                    float yr = 0.f, yi = 0.f;
-                    if (n < nr && j < bk.cols) {
-                        const cx<float> y = src.ptr[spos[jj] * src.ps + (r0 + n) * src.rs];
-                        yr = y.x;
-                        yi = y.y;
-                    }
-                    __nv_bfloat16 rh, rl, ih, il;
-                    split_bf16(yr, rh, rl);
-                    split_bf16(yi, ih, il);
-                    h0[u] = pack_bf16(rh, __hneg(ih));
-                    h1[u] = pack_bf16(ih, rh);
-                    l0[u] = pack_bf16(rl, __hneg(il));
-                    l1[u] = pack_bf16(il, rl);
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int s = g % S;
+                if (!mbar_wait(&bars->full[s], (uint32_t)(g / S) & 1, status)) {
+                    ok = false;
+                    break;
                 }
-                const int o0 = core_off(2 * n, 8 * jq, kTcK), o1 = core_off(2 * n + 1, 8 * jq, kTcK);
-                *reinterpret_cast<uint4*>(B0 + o0) = make_uint4(h0[0], h0[1], h0[2], h0[3]);
-                *reinterpret_cast<uint4*>(B0 + o1) = make_uint4(h1[0], h1[1], h1[2], h1[3]);
-                if (REFINE) {
-                    *reinterpret_cast<uint4*>(B0 + 2 * kTcMaxR * kTcK + o0) = make_uint4(l0[0], l0[1], l0[2], l0[3]);
-                    *reinterpret_cast<uint4*>(B0 + 2 * kTcMaxR * kTcK + o1) = make_uint4(l1[0], l1[1], l1[2], l1[3]);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;");
-            {
-                const bool w = mbar_wait(&fbar[s], loads[s] & 1);
-                ok = __syncthreads_and(w) != 0;
-                if (!ok) break;
-                loads[s]++;
-            }
-            if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t sbo = (kTcK / 8) * 128;
-                for (int kk = 0; kk < kTcK; kk += 16) {
-                    const uint32_t koff = (uint32_t)(kk / 8) * 128;
-                    const uint64_t ah = umma_desc(smem_u32(A0) + koff, 128, sbo);
-                    const uint64_t bh = umma_desc(smem_u32(B0) + koff, 128, sbo);
-                    umma_bf16(tmem, ah, bh, idesc, (c > 0 || kk > 0) ? 1u : 0u);
-                    if (REFINE) {
-                        const uint64_t al = umma_desc(smem_u32(A0 + kTcM * kTcK) + koff, 128, sbo);
-                        const uint64_t bl = umma_desc(smem_u32(B0 + 2 * kTcMaxR * kTcK) + koff, 128, sbo);
-                        umma_bf16(tmem, ah, bl, idesc, 1u);
-                        umma_bf16(tmem, al, bh, idesc, 1u);
+                if (lane == 0) {
+                    tc_issue_stage<REFINE>(tmem, ring + (size_t)s * Cfg::stage_elems, idesc, c == 0);
+                    umma_commit(&bars->empty[s]);
+                }
+                __syncwarp();
+                // chunk g + S - 1 takes the stage of chunk g - 1 once its MMAs are done
+                // (the MMAs of chunk g are queued behind them, so the tensor pipe stays fed)
+                if (g >= 1 && issued < total && issued == g + S - 1) {
+                    if (!mbar_wait(&bars->empty[(g - 1) % S], (uint32_t)((g - 1) / S) & 1, status)) {
+                        ok = false;
+                        break;
                     }
-                }
-                umma_commit(&mbar[s]);
-            }
-            commits[s]++;
-            pending[s] = true;
-        }
-        if (!ok) break;
-        {
-            const int last = (nchunk - 1) & 1;
-            const int order[2] = {last ^ 1, last};
-            for (int q = 0; q < 2 && ok; ++q) {
-                const int sw = order[q];
-                if (pending[sw]) {
-                    const bool w = mbar_wait(&mbar[sw], (commits[sw] - 1) & 1);
-                    ok = __syncthreads_and(w) != 0;
-                    if (ok) pending[sw] = false;
+                    copy(issued);
+                    ++issued;
                 }
             }
+            if (!ok) break;
+            if (lane == 0) umma_commit(&bars->done);
+            __syncwarp();
         }
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        {
-            const int wq = warp & 3;
-            const int rr = wq * 32 + lane;
-            const int ii = rt * kTcM + rr;
-            const int cbeg = (warp >> 2) * (N / 2), cend = cbeg + N / 2;
-            for (int c0 = cbeg; c0 < cend; c0 += 8) {
-                uint32_t v[8];
-                const uint32_t addr = tmem + ((uint32_t)(wq * 32) << 16) + (uint32_t)c0;
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7])
-                             : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                if (nchunk == 0) {
+        if (!ok && lane == 0) atomicExch(status, MIDBF_ETIMEOUT);
+        tc_mma_drain(&bars->fin, lane, status);
+        // copies that no producer waited for (after a timeout) land before the CTA exits
+        if (lane == 0) {
+            for (int gg = issued - 1; gg >= 0 && gg >= issued - S; --gg)
+                mbar_wait(&bars->aload[gg % S], (uint32_t)(gg / S) & 1, nullptr);
+        }
+        __syncwarp();
+    } else {
+        // ---- producers
+        const int ptid = tid;
+        const int row = ptid & (kTcM - 1);
+        const int i = rt * kTcM + row;
+        const bool rok = i < bk.rows;
+        const int op = rok ? st.out_pos[bk.out_off + i] : 0;
+        auto stage_pos = [&](int c, int slot) {
+            if (ptid < kTcKc) {
+                const int j = c * kTcKc + ptid;
+                spos[slot][ptid] = j < bk.cols ? st.in_pos[bk.in_off + j] : 0;
+            }
+        };
+        bool ok = true;
+        int g = 0;
+        for (int p = 0; p < npass && ok; ++p) {
+            const int r0 = p * kTcR;
+            const int R = min(kTcR, nrhs - r0), Rpad = (R + 15) & ~15;
+            TcBItems I;
+            tc_b_items(I, src, r0, R, Rpad, ptid);
+            TcBLoad Lcur, Lnext;
+            if (nchunk > 0) {
+                stage_pos(0, g % S);
+                producers_and(true);
+                tc_load_b(Lcur, I, spos[g % S], bk.cols, src);
+            }
+            for (int c = 0; c < nchunk; ++c, ++g) {
+                const int s = g % S, s1 = (g + 1) % S;
+                const bool more = c + 1 < nchunk;
+                if (more) stage_pos(c + 1, s1);
+                // the stage's A tiles have landed (and its previous MMAs are done: the
+                // copy was issued after them)
+                ok = producers_and(mbar_wait(&bars->aload[s], (uint32_t)(g / S) & 1, status));
+                if (!ok) break;
+                if (more) tc_load_b(Lnext, I, spos[s1], bk.cols - (c + 1) * kTcKc, src);
+                __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
+                // A_bot = (Im, Re) from A_top = (Re, -Im): 512 16-byte vectors per part
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = 0u;   // empty input side: the product is zero
+                for (int part = 0; part < NP; ++part) {
+                    const uint4 a = reinterpret_cast<const uint4*>(stg + part * kTcAElems)[ptid];
+                    reinterpret_cast<uint4*>(stg + (NP + part) * kTcAElems)[ptid] =
+                        make_uint4(top_to_bot(a.x), top_to_bot(a.y), top_to_bot(a.z), top_to_bot(a.w));
                 }
-                if (ii < bk.rows) {
-                    const int op = st.out_pos[bk.out_off + ii];
-#pragma unroll
-                    for (int q = 0; q < 8; q += 2) {
-                        const int n = (c0 + q) >> 1;
-                        if (n < nr)
-                            dst.ptr[op * dst.ps + (r0 + n) * dst.rs] =
-                                cx<float>{__uint_as_float(v[q]), __uint_as_float(v[q + 1])};
-                    }
-                }
+                tc_store_b<REFINE>(Lcur, I, stg + 2 * NP * kTcAElems);
+                asm volatile("fence.proxy.async.shared::cta;");
+                mbar_arrive(&bars->full[s]);
+                if (more) Lcur = Lnext;
             }
+            if (!ok) break;
+            ok = producers_and(mbar_wait(&bars->done, (uint32_t)p & 1, status));
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            tc_epilogue(tmem, warp, lane, Rpad, R, r0, rok, op, dst, nchunk == 0);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            mbar_arrive(&bars->tfree);
         }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!ok && ptid == 0) atomicExch(status, MIDBF_ETIMEOUT);
     }
-    if (!ok) {
-        if (tid == 0) atomicExch(status, MIDBF_ETIMEOUT);
-        for (int sw = 0; sw < 2; ++sw) {
-            if (pending[sw]) mbar_wait(&mbar[sw], (commits[sw] - 1) & 1);
-            if (issued[sw] > loads[sw]) mbar_wait(&fbar[sw], loads[sw] & 1);
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+    tc_teardown<S>(tmem, warp);
 }
 
 }  // namespace midbf_dev

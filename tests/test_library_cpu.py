@@ -56,6 +56,29 @@ def test_host_build_matches_direct_sum(n, family, n0):
     assert st["nx"] == n * n and st["nstages"] == 2 * st["nsteps"] + 1
 
 
+def test_fp32_storage_keeps_structure_and_accuracy():
+    """params.store_fp32 keeps the IDs' coefficients in complex FP32 on the
+    host: the same skeletons and ranks as the FP64 build, coefficients equal
+    to FP32 rounding, and the oracle's apply of the exported factors within
+    FP32 rounding of the FP64 plan's (and within the build tolerance of the
+    direct sum)."""
+    X, W, bx, bw = _grid(32)
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    p64 = mb.Plan.build(ph, tol=1e-6, n0=16, boxX=bx, boxW=bw)
+    p32 = mb.Plan.build(ph, tol=1e-6, n0=16, boxX=bx, boxW=bw, store_fp32=1)
+    assert p32.stats() == p64.stats()
+    f64, f32 = planio.read(p64.export()), planio.read(p32.export())
+    for s64, s32 in zip(f64.stages, f32.stages):
+        for b64, b32 in zip(s64.blocks, s32.blocks):
+            for u64, u32 in zip(b64.subs, b32.subs):
+                assert np.array_equal(u64.skel, u32.skel) and np.array_equal(u64.red, u32.red)
+                assert np.array_equal(u32.T, u64.T.astype(np.complex64).astype(np.complex128))
+    f = synth.complex_gaussian(32 * 32, 1, 0)[:, 0]
+    g64, g32 = midbf.apply(f64, f), midbf.apply(f32, f)
+    assert direct.rel_l2(g32, g64) < 1e-6
+    assert direct.rel_l2(g32, direct.direct_sum(OPhase(synth.PHASE_FIO2D, X, W), f)) < 2e-5
+
+
 def test_host_build_rank_one_exact_and_3d():
     X, W, bx, bw = _grid(32)
     for fam in (synth.PHASE_ZERO, synth.PHASE_SEPARABLE):
