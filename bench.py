@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="grid size of the 2D workloads")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
-    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump"],
+    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump", "batched"],
                     help="fio2d: 2D FIO phase on the n x n grid (--n, default 256); fio3d_n32: 3D, N = 32,768, "
                          "random X; fio2d_jump: 2D with the jump |xi| sign(x1 - 1/2) (--n, default 1024)")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's)")
@@ -128,17 +128,17 @@ PHASE_NAMES = {synth.PHASE_FIO2D: "FIO2D closed form", synth.PHASE_FIO3D: "FIO3D
                synth.PHASE_FIO2D_JUMP: "FIO2D + jump closed form"}
 
 
-def sampled_direct_error(ph, F, G, H, rows, cols, chunk=16):
+def sampled_direct_error(ph, F, G, Hin, H, rows, cols, chunk=16):
     """rel-L2 of sampled outputs against FP64 direct sums (eq. (1)).
 
-    G = K F and H = K^H G as computed on the GPU ((R, N) arrays); for the
+    G = K F and H = K^H Hin as computed on the GPU ((R, N) arrays); for the
     sampled rows i, sum_j exp(2 pi i Phi(x_i, xi_j)) F_j over every column j,
-    and for the sampled columns c, sum_i conj(exp(2 pi i Phi(x_i, xi_c))) G_i
+    and for the sampled columns c, sum_i conj(exp(2 pi i Phi(x_i, xi_c))) Hin_i
     over every row, with Phi from the library's FP64 phase evaluation (no part
-    of the apply path)."""
+    of the apply path).  Empty rows or cols give None for that direction."""
     nx, nw = ph.nx, ph.nw
     Fd = F.T.astype(np.complex128)
-    Gd = G.T.astype(np.complex128)
+    Gd = Hin.T.astype(np.complex128)
     num = den = 0.0
     for r0 in range(0, len(rows), chunk):
         rr = rows[r0:r0 + chunk]
@@ -148,7 +148,7 @@ def sampled_direct_error(ph, F, G, H, rows, cols, chunk=16):
         ref = K @ Fd
         num += np.sum(np.abs(G[:, rr].T - ref) ** 2)
         den += np.sum(np.abs(ref) ** 2)
-    e_fwd = math.sqrt(num / den)
+    e_fwd = math.sqrt(num / den) if len(rows) else None
     num = den = 0.0
     for c0 in range(0, len(cols), chunk):
         cc = cols[c0:c0 + chunk]
@@ -158,7 +158,7 @@ def sampled_direct_error(ph, F, G, H, rows, cols, chunk=16):
         ref = K @ Gd
         num += np.sum(np.abs(H[:, cc].T - ref) ** 2)
         den += np.sum(np.abs(ref) ** 2)
-    return e_fwd, math.sqrt(num / den)
+    return e_fwd, (math.sqrt(num / den) if len(cols) else None)
 
 
 class ClockSampler:
@@ -308,11 +308,148 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def main_batched(args, ws, rank, dev, pg):
+    """32 uneven instances (n from {64, 128, 256, 512}, 1..32 RHS, seed 1), each
+    applied forward and adjoint: one midbf_apply_batched call of 64 entries
+    per step, every plan autotuned for its RHS count."""
+    import torch
+    import paper_1908_09376_gb300 as mb
+    insts = synth.batched_instances(32, 1)
+    t0 = time.perf_counter()
+    dps, phs = [], []
+    for w in insts:
+        X, W, bx, bw = w.points()
+        ph = mb.Phase.closed_form(w.phase, X, W)
+        plan = mb.Plan.build(ph, tol=w.tol, n0=w.n0, boxX=bx, boxW=bw, nthreads=args.threads, device_ids=1,
+                             store_fp32=1)
+        dp = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY)
+        del plan
+        dps.append(dp)
+        phs.append(ph)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for dp, w in zip(dps, insts):
+        dp.autotune(w.nrhs)
+    t_tune = time.perf_counter() - t0
+    sel = dps + dps
+    adj = [0] * len(insts) + [1] * len(insts)
+    nr = [w.nrhs for w in insts] * 2
+    f_host = [synth.complex_gaussian(w.N, w.nrhs, w.f_seed) for w in insts]
+    h_host = [synth.complex_gaussian(w.N, w.nrhs, w.f_seed + 1000) for w in insts]
+    xs = [torch.from_numpy(a.T.copy()).to(dev, torch.complex64) for a in f_host + h_host]
+    outs = [torch.empty_like(x) for x in xs]
+    wsb = torch.empty(mb.batched_workspace_bytes(sel, nr), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        mb.apply_batched(sel, xs, adj, outs=outs, workspace=wsb)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    units = sum(2 * w.N * w.nrhs for w in insts)
+    ms_per_step, value = aggregate(sum(a.elapsed_time(b) for a, b in ev), units, args.steps, pg, dev)
+
+    # algorithmic bytes of one step: every instance's stages, forward and adjoint
+    total_bytes = 0.0
+    for dp, x, o, a in zip(sel, xs, outs, adj):
+        dp.profile(True)
+        dp.apply(x, adjoint=bool(a), out=o)
+        total_bytes += sum(by for _, _, by in dp.stage_times())
+        dp.profile(False)
+    peak, peak_kind = peaks()
+    achieved = total_bytes / (ms_per_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "kernel": "whole batched step",
+                "peak_source": peak_kind}
+
+    # per-instance accuracy against FP64 direct sums on 32 sampled rows / columns
+    step()
+    torch.cuda.synchronize()
+    errs = []
+    if rank == 0:
+        k = len(insts)
+        for i, w in enumerate(insts):
+            rows = synth.sample_rows(w.N, 32, w.sample_seed)
+            cols = synth.sample_rows(w.N, 32, w.sample_seed + 1)
+            G = outs[i].cpu().numpy()              # K f_i
+            A = outs[k + i].cpu().numpy()          # K^H h_i
+            e_f, e_a = sampled_direct_error(phs[i], f_host[i].T, G, h_host[i].T, A, rows, cols)
+            errs.append({"instance": w.name, "nrhs": w.nrhs, "forward": e_f, "adjoint": e_a})
+
+    # end to end: host inputs in pinned memory, copies inside the timed region
+    fh = [torch.from_numpy(a.T.astype(np.complex64).copy()).pin_memory() for a in f_host + h_host]
+    oh = [torch.empty(tuple(o.shape), dtype=o.dtype).pin_memory() for o in outs]
+    ke = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(ke):
+        for x, a in zip(xs, fh):
+            x.copy_(a, non_blocking=True)
+        step()
+        for o, a in zip(outs, oh):
+            a.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - te) / ke
+    io_bytes = sum(x.numel() * 8 for x in xs)
+    e2e = {"value": ws * units / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": io_bytes,
+           "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_s * 1e3, 4)}
+    launches = mb.batched_launches(sel, adj, nr)
+    counts = {}
+    for w in insts:
+        counts[w.n] = counts.get(w.n, 0) + 1
+    out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": "batched32_fio2d", "instances": len(insts), "n_counts": counts,
+                      "nrhs": [w.nrhs for w in insts], "points_rhs_per_step": units, "mode": "fp32",
+                      "step": "forward + adjoint of every instance in one midbf_apply_batched call",
+                      "tol": 1e-6, "n0": 64, "build": "device", "store": "fp32", "autotuned": True,
+                      "build_s": round(t_build, 1), "tune_s": round(t_tune, 1),
+                      "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas x{ws}"},
+           "roofline": roofline, "rel_l2_direct_sampled": {"max_forward": max(e["forward"] for e in errs) if errs else None,
+                                                           "max_adjoint": max(e["adjoint"] for e in errs) if errs else None,
+                                                           "rows": 32, "per_instance": errs},
+           "clocks": clk, "e2e": e2e, "gpu_launches": args.steps * launches, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "batched":
+        import torch
+        torch.cuda.set_device(local)
+        dev = torch.device("cuda", local)
+        pg = None
+        if ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=dev)
+            pg = dist
+        main_batched(args, ws, rank, dev, pg)
+        if pg:
+            pg.destroy_process_group()
         return
     import torch
     import paper_1908_09376_gb300 as mb
@@ -350,7 +487,7 @@ def main():
     ws1 = torch.empty(dp32.workspace_bytes(R1), dtype=torch.uint8, device=dev)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-    launches_per_apply = dp32.launches()
+    launches_per_apply = dp32.launches(R1)
 
     t_tune = 0.0
     if tune:
@@ -458,7 +595,7 @@ def main():
         Hn = h.reshape(R1, N).cpu().numpy()
         rows = synth.sample_rows(N, wl.sample_rows, wl.sample_seed)
         cols = synth.sample_rows(N, wl.sample_rows, wl.sample_seed + 1)
-        e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Hn, rows, cols)
+        e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Gn, Hn, rows, cols)
         acc = {"forward": e_f, "adjoint": e_a, "rows": int(wl.sample_rows),
                "reference": "FP64 direct sum over all columns (rows) for sampled outputs"}
 

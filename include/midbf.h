@@ -245,6 +245,10 @@ int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, vo
  * an output.  workspace: device memory of midbf_batched_workspace_size bytes.
  * Errors: MIDBF_EINVAL, MIDBF_ECUDA. */
 int midbf_batched_workspace_size(int count, const midbf_dplan* const* dps, const int* nrhs, size_t* bytes);
+/* Number of kernel launches midbf_apply_batched issues for these instances,
+ * directions and RHS counts (no device work).  Errors: MIDBF_EINVAL. */
+int midbf_batched_launches(int count, const midbf_dplan* const* dps, const int* adjoint, const int* nrhs,
+                           int* launches);
 int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adjoint,
                         const void* const* in, const int64_t* ldin, void* const* out,
                         const int64_t* ldout, const int* nrhs, void* stream,
@@ -310,7 +314,10 @@ int midbf_autotune(midbf_dplan* dp, int nrhs, void* stream);
 int midbf_set_choice(midbf_dplan* dp, int nrhs, int stage, int adjoint, int choice);
 int midbf_get_choice(const midbf_dplan* dp, int nrhs, int stage, int adjoint, int* choice);
 
-/* Number of kernel launches one midbf_apply issues (for launch accounting). */
+/* Number of kernel launches one forward midbf_apply with nrhs right-hand
+ * sides issues (for launch accounting): one per stage, two (pack, multiply)
+ * per group of 256 RHS for a stage on the tensor cores.  EINVAL on a null
+ * argument or nrhs <= 0. */
 int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches);
 
 /* Per-stage timing for measurement: with enable = 1, every later midbf_apply

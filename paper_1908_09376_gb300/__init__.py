@@ -108,6 +108,8 @@ midbf_stage_info = _sig("midbf_stage_info", C.c_int,
                         [_vp, C.c_int, C.POINTER(C.c_int), _i64p, _i64p, C.POINTER(C.c_int)])
 midbf_batched_workspace_size = _sig("midbf_batched_workspace_size", C.c_int,
                                     [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_size_t)])
+midbf_batched_launches = _sig("midbf_batched_launches", C.c_int,
+                              [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)])
 midbf_apply_batched = _sig("midbf_apply_batched", C.c_int,
                            [C.c_int, C.POINTER(_vp), C.POINTER(C.c_int), C.POINTER(_vp), _i64p, C.POINTER(_vp),
                             _i64p, C.POINTER(C.c_int), _vp, _vp, C.c_size_t])
@@ -442,6 +444,26 @@ class capture:
         elif rc == OK:
             midbf_graph_destroy(h)
         return False
+
+
+def batched_launches(dplans, adjoints, nrhs):
+    """Kernel launches one apply_batched call issues for these instances."""
+    n = len(dplans)
+    hs = (_vp * n)(*[d.h.value for d in dplans])
+    adj = (C.c_int * n)(*[int(a) for a in adjoints])
+    nr = (C.c_int * n)(*[int(r) for r in nrhs])
+    out = C.c_int()
+    check(midbf_batched_launches(n, hs, adj, nr, C.byref(out)), "midbf_batched_launches")
+    return out.value
+
+
+def batched_workspace_bytes(dplans, nrhs):
+    n = len(dplans)
+    hs = (_vp * n)(*[d.h.value for d in dplans])
+    nr = (C.c_int * n)(*[int(r) for r in nrhs])
+    need = C.c_size_t()
+    check(midbf_batched_workspace_size(n, hs, nr, C.byref(need)), "midbf_batched_workspace_size")
+    return need.value
 
 
 def apply_batched(dplans, xs, adjoints, outs=None, workspace=None, stream=None):

@@ -72,6 +72,9 @@ struct DevStage : DevStageBase {
     TcStage tcs[2]{};
     int n_tc_items[2] = {0, 0};
     double tc_bytes[2] = {0, 0};
+    // B-image chunks of the stage input, per orientation (V/U and middle factor)
+    TcPack pk[2]{};
+    const int* chunk0_s[2] = {nullptr, nullptr};   // middle factor: first chunk of each block
 };
 
 }  // namespace
@@ -86,6 +89,7 @@ struct midbf_dplan {
     int64_t max_space = 0;        // longest internal vector space
     size_t factor_bytes = 0, index_bytes = 0;
     size_t tc_image_bytes = 0;    // dense BF16 tile images (tensor-core modes)
+    int max_tc_chunks = 0;        // most B-image chunks of one tensor-core stage launch
     std::vector<void*> allocs;
     std::vector<DevStage<float>> st32;
     std::vector<DevStage<double>> st64;
@@ -167,7 +171,7 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
     for (int o = 0; o < 2; ++o) {
         std::vector<TcBlock> tb(nb);
         std::vector<int> ipos, opos;
-        std::vector<int2> items;
+        std::vector<int2> items, chunks;
         long long off = 0;
         for (int b = 0; b < nb; ++b) {
             const Block& bk = st.blocks[b];
@@ -176,12 +180,14 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
             TcBlock& t = tb[b];
             t.rows = (int)dst.size();
             t.cols = (int)src.size();
-            t.in_off = (int)ipos.size();
             t.out_off = (int)opos.size();
+            t.chunk0 = (int)chunks.size();
             t.img_off = off;
+            const int in_off = (int)ipos.size();
             for (int64_t v : src) ipos.push_back((int)v);
             for (int64_t v : dst) opos.push_back((int)v);
             const int nrt = (t.rows + kTcM - 1) / kTcM, nch = (t.cols + kTcKc - 1) / kTcKc;
+            for (int c = 0; c < nch; ++c) chunks.push_back(make_int2(in_off + c * kTcKc, std::min(kTcKc, t.cols - c * kTcKc)));
             for (int r = 0; r < nrt; ++r) items.push_back(make_int2(b, r));
             off += (long long)nrt * nch * NP * kTcTileElems;
         }
@@ -230,8 +236,11 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
             });
         for (auto& t : th) t.join();
         ds.tcs[o].blocks = upload(dp, tb, &dp->index_bytes);
-        ds.tcs[o].in_pos = upload(dp, ipos, &dp->index_bytes);
         ds.tcs[o].out_pos = upload(dp, opos, &dp->index_bytes);
+        ds.pk[o].pos = upload(dp, ipos, &dp->index_bytes);
+        ds.pk[o].chunks = upload(dp, chunks, &dp->index_bytes);
+        ds.pk[o].nchunks = (int)chunks.size();
+        dp->max_tc_chunks = std::max(dp->max_tc_chunks, (int)chunks.size());
         ds.tcs[o].items = upload(dp, items, &dp->index_bytes);
         ds.tcs[o].img = reinterpret_cast<const __nv_bfloat16*>(upload(dp, img, &dp->tc_image_bytes));
         ds.n_tc_items[o] = (int)items.size();
@@ -522,6 +531,28 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     ds.n_items_cols = (int)it_cols.size();
     ds.n_items_rows4 = (int)it_rows4.size();
     ds.n_items_cols4 = (int)it_cols4.size();
+    if constexpr (sizeof(R) == 4) {
+        if (dp->tc_mode) {
+            // B-image chunks of the middle factor's input: forward the columns
+            // (Omega side) of each block, adjoint its rows (X side)
+            for (int o = 0; o < 2; ++o) {
+                const std::vector<int>& off = o == 0 ? blk_cols : blk_rows;
+                const std::vector<int>& cnt = o == 0 ? blk_ncol : blk_nrow;
+                std::vector<int2> chunks;
+                std::vector<int> c0(st.blocks.size());
+                for (size_t b = 0; b < st.blocks.size(); ++b) {
+                    c0[b] = (int)chunks.size();
+                    for (int c = 0; c * kTcKc < cnt[b]; ++c)
+                        chunks.push_back(make_int2(off[b] + c * kTcKc, std::min(kTcKc, cnt[b] - c * kTcKc)));
+                }
+                ds.pk[o].pos = o == 0 ? ds.scols.pos : ds.srows.pos;
+                ds.pk[o].chunks = upload(dp, chunks, &dp->index_bytes);
+                ds.pk[o].nchunks = (int)chunks.size();
+                ds.chunk0_s[o] = upload(dp, c0, &dp->index_bytes);
+                dp->max_tc_chunks = std::max(dp->max_tc_chunks, (int)chunks.size());
+            }
+        }
+    }
 }
 
 template <class R>
@@ -784,8 +815,24 @@ void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
 constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
 constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
 
+// Tensor-core stages run in groups of at most kTcR RHS.  Each group first
+// packs the stage input into per-chunk B images (k_pack_b, in the workspace
+// area tc_bimg) and then multiplies.
+inline VecRef<float> rhs_shift(VecRef<float> v, int r0) {
+    v.ptr += (long long)r0 * v.rs;
+    return v;
+}
+
+void launch_pack(const TcPack& pk, VecRef<float> src, int R, bool refine, __nv_bfloat16* bimg, cudaStream_t s) {
+    if (pk.nchunks == 0) return;
+    const int Rpad = (R + 15) & ~15;
+    const int grid = std::min(pk.nchunks, 152 * 8);
+    if (refine) k_pack_b<true><<<grid, 256, 0, s>>>(pk, src, R, Rpad, bimg);
+    else k_pack_b<false><<<grid, 256, 0, s>>>(pk, src, R, Rpad, bimg);
+}
+
 template <int PQ, bool RF, bool CJ>
-void launch_tc_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
+void launch_tc_t(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv_bfloat16* bimg, int* status,
                  cudaStream_t s) {
     SStage<float> st = ds.ss;
     const size_t sm = tc_smem_bytes<RF>();
@@ -793,54 +840,81 @@ void launch_tc_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst
     set_smem(kf, sm);
     if (!CJ) {
         st.items = ds.items_rows4;
-        kf<<<ds.n_items_rows4, kTcThreads, sm, s>>>(st, ds.srows, ds.scols, src, dst, nrhs, 1, status);
+        kf<<<ds.n_items_rows4, kTcThreads, sm, s>>>(st, ds.srows, ds.scols, ds.chunk0_s[0], bimg, dst, R, 1, status);
     } else {
         st.items = ds.items_cols4;
-        kf<<<ds.n_items_cols4, kTcThreads, sm, s>>>(st, ds.scols, ds.srows, src, dst, nrhs, 0, status);
+        kf<<<ds.n_items_cols4, kTcThreads, sm, s>>>(st, ds.scols, ds.srows, ds.chunk0_s[1], bimg, dst, R, 0, status);
     }
 }
 
 template <bool RF, bool CJ>
-void launch_tc_rc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
+void launch_tc_rc(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv_bfloat16* bimg, int* status,
                   cudaStream_t s) {
     switch (phase_shape_code(ds.ss.P, ds.ss.Q)) {
-        case 1: launch_tc_t<1, RF, CJ>(ds, src, dst, nrhs, status, s); break;
-        case 2: launch_tc_t<2, RF, CJ>(ds, src, dst, nrhs, status, s); break;
-        case 3: launch_tc_t<3, RF, CJ>(ds, src, dst, nrhs, status, s); break;
-        case 4: launch_tc_t<4, RF, CJ>(ds, src, dst, nrhs, status, s); break;
-        case 5: launch_tc_t<5, RF, CJ>(ds, src, dst, nrhs, status, s); break;
-        default: launch_tc_t<0, RF, CJ>(ds, src, dst, nrhs, status, s);
+        case 1: launch_tc_t<1, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        case 2: launch_tc_t<2, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        case 3: launch_tc_t<3, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        case 4: launch_tc_t<4, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        case 5: launch_tc_t<5, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        default: launch_tc_t<0, RF, CJ>(ds, dst, R, bimg, status, s);
     }
 }
 
+// Middle factor on the tensor cores.
 void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint, bool refine,
-               int* status, cudaStream_t s) {
-    if (refine) {
-        if (adjoint) launch_tc_rc<true, true>(ds, src, dst, nrhs, status, s);
-        else launch_tc_rc<true, false>(ds, src, dst, nrhs, status, s);
-    } else {
-        if (adjoint) launch_tc_rc<false, true>(ds, src, dst, nrhs, status, s);
-        else launch_tc_rc<false, false>(ds, src, dst, nrhs, status, s);
+               __nv_bfloat16* bimg, int* status, cudaStream_t s) {
+    const int o = adjoint ? 1 : 0;
+    for (int r0 = 0; r0 < nrhs; r0 += kTcR) {
+        const int R = std::min(kTcR, nrhs - r0);
+        launch_pack(ds.pk[o], rhs_shift(src, r0), R, refine, bimg, s);
+        const VecRef<float> d = rhs_shift(dst, r0);
+        if (refine) {
+            if (adjoint) launch_tc_rc<true, true>(ds, d, R, bimg, status, s);
+            else launch_tc_rc<true, false>(ds, d, R, bimg, status, s);
+        } else {
+            if (adjoint) launch_tc_rc<false, true>(ds, d, R, bimg, status, s);
+            else launch_tc_rc<false, false>(ds, d, R, bimg, status, s);
+        }
     }
     CK(cudaGetLastError());
-}
-
-template <bool RF>
-void launch_blk_tc_t(const TcStage& st, int items, VecRef<float> src, VecRef<float> dst, int nrhs, int* status,
-                     cudaStream_t s) {
-    const size_t sm = tc_smem_bytes<RF>();
-    auto kf = k_blk_tc<RF>;
-    set_smem(kf, sm);
-    kf<<<items, kTcThreads, sm, s>>>(st, src, dst, nrhs, status);
 }
 
 // V / U stage on the tensor cores: o = 0 forward, 1 adjoint orientation.
 void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<float> dst, int nrhs, bool refine,
-                   int* status, cudaStream_t s) {
+                   __nv_bfloat16* bimg, int* status, cudaStream_t s) {
     if (ds.n_tc_items[o] == 0) return;
-    if (refine) launch_blk_tc_t<true>(ds.tcs[o], ds.n_tc_items[o], src, dst, nrhs, status, s);
-    else launch_blk_tc_t<false>(ds.tcs[o], ds.n_tc_items[o], src, dst, nrhs, status, s);
+    const size_t sm = refine ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
+    for (int r0 = 0; r0 < nrhs; r0 += kTcR) {
+        const int R = std::min(kTcR, nrhs - r0);
+        launch_pack(ds.pk[o], rhs_shift(src, r0), R, refine, bimg, s);
+        const VecRef<float> d = rhs_shift(dst, r0);
+        if (refine) {
+            auto kf = k_blk_tc<true>;
+            set_smem(kf, sm);
+            kf<<<ds.n_tc_items[o], kTcThreads, sm, s>>>(ds.tcs[o], bimg, d, R, status);
+        } else {
+            auto kf = k_blk_tc<false>;
+            set_smem(kf, sm);
+            kf<<<ds.n_tc_items[o], kTcThreads, sm, s>>>(ds.tcs[o], bimg, d, R, status);
+        }
+    }
     CK(cudaGetLastError());
+}
+
+// Bytes of the B-image area of the workspace for nrhs RHS (0 outside the
+// tensor-core modes): the largest stage's chunks at one group of <= kTcR RHS.
+// Bytes of the two ping-pong vectors of the workspace, rounded up to 256.
+size_t vec_workspace_bytes(const midbf_dplan* dp, int nrhs) {
+    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    return (b + 255) / 256 * 256;
+}
+
+size_t tc_bimg_bytes(const midbf_dplan* dp, int nrhs) {
+    if (!dp->tc_mode || dp->max_tc_chunks == 0) return 0;
+    const int Rpad = (std::min(nrhs, kTcR) + 15) & ~15;
+    const size_t b = (size_t)dp->max_tc_chunks * tc_bimg_elems(Rpad, dp->tc_mode == 2) * 2;
+    return (b + 255) / 256 * 256;
 }
 
 template <class R>
@@ -870,14 +944,14 @@ inline bool valid_choice(int choice) {
 // MIDBF_CHOICE_PERSIST, or MIDBF_CHOICE_TENSOR.
 template <class R>
 void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, VecRef<R> src, VecRef<R> dst, int nrhs,
-                  int choice, cudaStream_t s) {
+                  int choice, __nv_bfloat16* bimg, cudaStream_t s) {
     if constexpr (sizeof(R) == 4) {
         const bool tc_ok = ds.id ? ds.tc : dp->tc_mode != 0;
         const bool use_tc = tc_ok && (choice == MIDBF_CHOICE_TENSOR ||
                                       (choice == MIDBF_CHOICE_DEFAULT && nrhs >= (ds.id ? kTcBlkMinRhs : kTcMinRhs)));
         if (use_tc) {
-            if (ds.id) launch_blk_tc(ds, adjoint ? 1 : 0, src, dst, nrhs, dp->tc_mode == 2, dp->d_status, s);
-            else launch_tc(ds, src, dst, nrhs, adjoint, dp->tc_mode == 2, dp->d_status, s);
+            if (ds.id) launch_blk_tc(ds, adjoint ? 1 : 0, src, dst, nrhs, dp->tc_mode == 2, bimg, dp->d_status, s);
+            else launch_tc(ds, src, dst, nrhs, adjoint, dp->tc_mode == 2, bimg, dp->d_status, s);
             return;
         }
     }
@@ -905,6 +979,7 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
          void* out, int64_t ldout, int nrhs, cudaStream_t s, void* ws) {
     const int ns = (int)stages.size();
     cx<R>* buf[2] = {static_cast<cx<R>*>(ws), static_cast<cx<R>*>(ws) + dp->max_space * nrhs};
+    __nv_bfloat16* bimg = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(ws) + vec_workspace_bytes(dp, nrhs));
     VecRef<R> uin{(cx<R>*)in, 1, ldin};
     VecRef<R> uout{(cx<R>*)out, 1, ldout};
     auto internal = [&](int space) { return VecRef<R>{buf[space & 1], nrhs, 1}; };
@@ -929,7 +1004,7 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
         VecRef<R> fout = ds.out_user ? (adjoint ? uin : uout) : internal(sidx);
         VecRef<R> src = adjoint ? fout : fin;
         VecRef<R> dst = adjoint ? fin : fout;
-        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, tuned_choice(dp, nrhs, sidx, adjoint), s);
+        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, tuned_choice(dp, nrhs, sidx, adjoint), bimg, s);
         if (dp->profile) CK(cudaEventRecord(dp->ev[2 * q + 1], s));
     }
 }
@@ -1085,15 +1160,19 @@ void launch_batch_group(const midbf_dplan* const* dps, const std::array<int, 4>&
 }
 
 template <class R>
-void run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
-                 const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, cudaStream_t s,
-                 char* ws) {
+// Returns the number of launches; dry = true only counts them.
+int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
+                const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, cudaStream_t s,
+                char* ws, bool dry = false) {
+    int launches = 0;
     std::vector<cx<R>*> b0(count), b1(count);
     size_t off = 0;
     int maxst = 0;
     for (int i = 0; i < count; ++i) {
-        b0[i] = reinterpret_cast<cx<R>*>(ws + off);
-        b1[i] = b0[i] + dps[i]->max_space * nrhs[i];
+        if (!dry) {
+            b0[i] = reinterpret_cast<cx<R>*>(ws + off);
+            b1[i] = b0[i] + dps[i]->max_space * nrhs[i];
+        }
         off += instance_workspace(dps[i], nrhs[i]);
         maxst = std::max(maxst, (int)stages_of<R>(dps[i]).size());
     }
@@ -1143,10 +1222,12 @@ void run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, c
             const auto& ents = kv.second;
             for (size_t g0 = 0; g0 < ents.size(); g0 += kBatch) {
                 const int n = (int)std::min<size_t>(kBatch, ents.size() - g0);
-                launch_batch_group<R>(dps, key, &ents[g0], n, nrhs, adjoint, s);
+                if (!dry) launch_batch_group<R>(dps, key, &ents[g0], n, nrhs, adjoint, s);
+                ++launches;
             }
         }
     }
+    return launches;
 }
 
 int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint) {
@@ -1193,16 +1274,19 @@ void autotune(midbf_dplan* dp, const std::vector<DevStage<R>>& stages, int nrhs,
     const size_t ce = sizeof(cx<R>);
     const int64_t nuser = std::max(dp->nx, dp->nw);
     const size_t ub = (size_t)nuser * nrhs * ce, ib = (size_t)std::max<int64_t>(dp->max_space, 1) * nrhs * ce;
+    const size_t bb = tc_bimg_bytes(dp, nrhs);
     void* mem = nullptr;
-    if (cudaMalloc(&mem, 2 * ub + 2 * ib) != cudaSuccess) fail(MIDBF_ENOMEM, "autotune: cudaMalloc of the trial vectors failed");
+    if (cudaMalloc(&mem, 2 * ub + 2 * ib + bb) != cudaSuccess)
+        fail(MIDBF_ENOMEM, "autotune: cudaMalloc of the trial vectors failed");
     struct Free {
         void* p;
         ~Free() { cudaFree(p); }
     } guard{mem};
-    CK(cudaMemsetAsync(mem, 0, 2 * ub + 2 * ib, s));
+    CK(cudaMemsetAsync(mem, 0, 2 * ub + 2 * ib + bb, s));
     cx<R>* ubuf[2] = {static_cast<cx<R>*>(mem), reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + ub)};
     cx<R>* ibuf[2] = {reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + 2 * ub),
                       reinterpret_cast<cx<R>*>(static_cast<char*>(mem) + 2 * ub + ib)};
+    __nv_bfloat16* bimg = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(mem) + 2 * ub + 2 * ib);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1219,11 +1303,11 @@ void autotune(midbf_dplan* dp, const std::vector<DevStage<R>>& stages, int nrhs,
                 VecRef<R> src = adjoint ? fout : fin, dst = adjoint ? fin : fout;
                 float best_ms = 1e30f;
                 for (int cand : stage_candidates<R>(dp, ds, adjoint, nrhs)) {
-                    launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, s);
+                    launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, bimg, s);
                     float t = 1e30f;
                     for (int rep = 0; rep < 3; ++rep) {
                         CK(cudaEventRecord(e0, s));
-                        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, s);
+                        launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, cand, bimg, s);
                         CK(cudaEventRecord(e1, s));
                         CK(cudaEventSynchronize(e1));
                         float ms = 0.f;
@@ -1415,8 +1499,7 @@ int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes) {
         set_last_error("midbf_workspace_size: bad argument");
         return MIDBF_EINVAL;
     }
-    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-    *bytes = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    *bytes = vec_workspace_bytes(dp, nrhs) + tc_bimg_bytes(dp, nrhs);
     return MIDBF_OK;
 }
 
@@ -1431,12 +1514,30 @@ int midbf_dplan_bytes(const midbf_dplan* dp, size_t* factor_bytes, size_t* index
 }
 
 int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches) {
-    (void)nrhs;
-    if (!dp || !launches) {
+    if (!dp || !launches || nrhs <= 0) {
         set_last_error("midbf_apply_launches: bad argument");
         return MIDBF_EINVAL;
     }
-    *launches = dp->launches;
+    // mirrors launch_stage: a tensor-core stage runs a pack and a multiply per
+    // group of kTcR RHS, a SIMT stage one launch
+    int n = 0;
+    const int groups = (nrhs + kTcR - 1) / kTcR;
+    auto count = [&](const auto& stages) {
+        for (size_t q = 0; q < stages.size(); ++q) {
+            const auto& ds = stages[q];
+            const int ch = tuned_choice(dp, nrhs, (int)q, false);
+            bool tc = false;
+            if (dp->precision == MIDBF_FP32) {
+                const bool tc_ok = ds.id ? ds.tc : dp->tc_mode != 0;
+                tc = tc_ok && (ch == MIDBF_CHOICE_TENSOR ||
+                               (ch == MIDBF_CHOICE_DEFAULT && nrhs >= (ds.id ? kTcBlkMinRhs : kTcMinRhs)));
+            }
+            n += tc ? 2 * groups : 1;
+        }
+    };
+    if (dp->precision == MIDBF_FP32) count(dp->st32);
+    else count(dp->st64);
+    *launches = n;
     return MIDBF_OK;
 }
 
@@ -1534,6 +1635,28 @@ int midbf_batched_workspace_size(int count, const midbf_dplan* const* dps, const
     }
     *bytes = b;
     return MIDBF_OK;
+}
+
+int midbf_batched_launches(int count, const midbf_dplan* const* dps, const int* adjoint, const int* nrhs,
+                           int* launches) {
+    try {
+        if (count <= 0 || !dps || !adjoint || !nrhs || !launches) fail(MIDBF_EINVAL, "null argument");
+        const int prec = dps[0] ? dps[0]->precision : -1;
+        for (int i = 0; i < count; ++i)
+            if (!dps[i] || nrhs[i] <= 0 || dps[i]->precision != prec) fail(MIDBF_EINVAL, "bad instance " + std::to_string(i));
+        std::vector<const void*> in(count, nullptr);
+        std::vector<void*> out(count, nullptr);
+        std::vector<int64_t> ld(count, 0);
+        *launches = prec == MIDBF_FP32
+                        ? run_batched<float>(count, dps, adjoint, in.data(), ld.data(), out.data(), ld.data(), nrhs,
+                                             nullptr, nullptr, true)
+                        : run_batched<double>(count, dps, adjoint, in.data(), ld.data(), out.data(), ld.data(), nrhs,
+                                              nullptr, nullptr, true);
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
 }
 
 int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,

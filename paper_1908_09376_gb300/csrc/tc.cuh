@@ -183,18 +183,24 @@ template <int S>
 struct TcBars {
     uint64_t full[S];    // producers -> MMA warp (count kTcProducers)
     uint64_t empty[S];   // MMAs of the stage complete (tcgen05.commit)
-    uint64_t aload[S];   // bulk copy of the stage's A tiles landed (k_blk_tc)
-    uint64_t done;       // all MMAs of a pass complete
-    uint64_t tfree;      // the epilogue of a pass has read TMEM (count kTcProducers)
+    uint64_t load[S];    // bulk copies into the stage landed (B image; A tile in k_blk_tc)
+    uint64_t done;       // all MMAs complete
     uint64_t fin;        // teardown: every MMA issued has completed
     uint32_t taddr;
 };
 
+// B image of one chunk: NP parts (hi, lo) of Rpad rows (RHS) x 32 (16 complex
+// columns, re/im interleaved) in the core-matrix layout.
+__host__ __device__ inline size_t tc_bimg_elems(int Rpad, bool refine) {
+    return (size_t)(refine ? 2 : 1) * (size_t)Rpad * kTcK;
+}
+
 // MMAs of one ring stage: D_top += A_top B^T and D_bot += A_bot B^T over the
-// stage's K = 32, plus the hi/lo refinement products.
+// stage's K = 32, plus the hi/lo refinement products.  The B lo part sits
+// b_lo bytes after the B hi part.
 template <bool REFINE>
 __device__ __forceinline__ void tc_issue_stage(uint32_t tmem, const __nv_bfloat16* stage, uint32_t idesc,
-                                               bool first) {
+                                               uint32_t b_lo, bool first) {
     constexpr int NP = REFINE ? 2 : 1;
     constexpr uint32_t sbo = (kTcK / 8) * 128;
     const uint32_t aT = smem_u32(stage);
@@ -210,7 +216,7 @@ __device__ __forceinline__ void tc_issue_stage(uint32_t tmem, const __nv_bfloat1
         umma_bf16(tmem, th, bh, idesc, acc);
         umma_bf16(tmem + kTcR, uh, bh, idesc, acc);
         if (REFINE) {
-            const uint64_t bl = umma_desc(bB + kTcBElems * 2 + ko, 128, sbo);
+            const uint64_t bl = umma_desc(bB + b_lo + ko, 128, sbo);
             const uint64_t tl = umma_desc(aT + kTcAElems * 2 + ko, 128, sbo);
             const uint64_t ul = umma_desc(aB + kTcAElems * 2 + ko, 128, sbo);
             umma_bf16(tmem, th, bl, idesc, 1u);
@@ -221,74 +227,51 @@ __device__ __forceinline__ void tc_issue_stage(uint32_t tmem, const __nv_bfloat1
     }
 }
 
-// Right-hand sides of one ring stage: rows n < Rpad of B from the stage's 16
-// columns at positions pos[0..16) of src (zero past ncol_left or R).  Item e
-// = (n, quad jq): 4 consecutive columns of RHS n = one 16-byte core row;
-// consecutive threads take consecutive RHS.  The item coordinates depend on
-// the pass only, so they are set once per pass (TcBItems).
-constexpr int kTcBItems = (kTcR * kTcKc / 4 + kTcProducers - 1) / kTcProducers;  // items per thread
-
-struct TcBItems {
-    int n[kTcBItems], jq[kTcBItems];
-    long long roff[kTcBItems];   // (r0 + n) * rs
-    bool on[kTcBItems];          // item exists (e < Rpad * 4)
-    bool live[kTcBItems];        // RHS exists (n < R)
+// ---------------------------------------------------------------------------
+// Right-hand sides.  Before a tensor-core stage runs, k_pack_b gathers its
+// input once per (block, 16-column chunk) and writes the chunk's B image:
+// row n = RHS n, (Re y, Im y) of the 16 columns interleaved along K, BF16 hi
+// (and lo) in the core-matrix layout, so that the MMA warp moves it with one
+// bulk copy.  Chunk q holds the columns at positions pos[chunks[q].x + j],
+// j < chunks[q].y (<= 16); the rest of the chunk is zero.
+struct TcPack {
+    const int2* chunks;
+    const int* pos;
+    int nchunks;
 };
-
-__device__ __forceinline__ void tc_b_items(TcBItems& I, VecRef<float> src, int r0, int R, int Rpad, int ptid) {
-#pragma unroll
-    for (int it = 0; it < kTcBItems; ++it) {
-        const int e = ptid + it * kTcProducers;
-        I.on[it] = e < Rpad * 4;
-        I.n[it] = e % Rpad;
-        I.jq[it] = e / Rpad;
-        I.live[it] = I.on[it] && I.n[it] < R;
-        I.roff[it] = (long long)(r0 + I.n[it]) * src.rs;
-    }
-}
-
-struct TcBLoad {
-    float2 y[kTcBItems][4];
-};
-
-__device__ __forceinline__ void tc_load_b(TcBLoad& L, const TcBItems& I, const int* pos, int ncol_left,
-                                          VecRef<float> src) {
-#pragma unroll
-    for (int it = 0; it < kTcBItems; ++it) {
-        const int4 p4 = *reinterpret_cast<const int4*>(pos + 4 * (I.jq[it] & 3));
-        const int pp[4] = {p4.x, p4.y, p4.z, p4.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            float2 v = make_float2(0.f, 0.f);
-            if (I.live[it] && I.jq[it] * 4 + u < ncol_left) {
-                const cx<float> y = src.ptr[(long long)pp[u] * src.ps + I.roff[it]];
-                v = make_float2(y.x, y.y);
-            }
-            L.y[it][u] = v;
-        }
-    }
-}
 
 template <bool REFINE>
-__device__ __forceinline__ void tc_store_b(const TcBLoad& L, const TcBItems& I, __nv_bfloat16* B) {
-#pragma unroll
-    for (int it = 0; it < kTcBItems; ++it) {
-        if (I.on[it]) {
+__global__ void __launch_bounds__(256) k_pack_b(TcPack pk, VecRef<float> src, int R, int Rpad, __nv_bfloat16* img) {
+    const size_t ce = tc_bimg_elems(Rpad, REFINE);
+    for (int q = blockIdx.x; q < pk.nchunks; q += gridDim.x) {
+        const int2 ch = pk.chunks[q];
+        __nv_bfloat16* out = img + (size_t)q * ce;
+        for (int e = threadIdx.x; e < Rpad * 4; e += blockDim.x) {
+            const int n = e % Rpad, jq = e / Rpad;   // consecutive threads: consecutive RHS
             uint32_t h[4], l[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) split_pair(L.y[it][u].x, L.y[it][u].y, h[u], l[u]);
-            const int o = core_off(I.n[it], 8 * I.jq[it], kTcK);
-            *reinterpret_cast<uint4*>(B + o) = make_uint4(h[0], h[1], h[2], h[3]);
-            if (REFINE) *reinterpret_cast<uint4*>(B + kTcBElems + o) = make_uint4(l[0], l[1], l[2], l[3]);
+            for (int u = 0; u < 4; ++u) {
+                const int jj = jq * 4 + u;
+                float re = 0.f, im = 0.f;
+                if (n < R && jj < ch.y) {
+                    const cx<float> y = src.ptr[(long long)__ldg(pk.pos + ch.x + jj) * src.ps + (long long)n * src.rs];
+                    re = y.x;
+                    im = y.y;
+                }
+                split_pair(re, im, h[u], l[u]);
+            }
+            const int o = core_off(n, 8 * jq, kTcK);
+            *reinterpret_cast<uint4*>(out + o) = make_uint4(h[0], h[1], h[2], h[3]);
+            if (REFINE) *reinterpret_cast<uint4*>(out + (size_t)Rpad * kTcK + o) = make_uint4(l[0], l[1], l[2], l[3]);
         }
     }
 }
 
-// Epilogue of a pass: producer warp w reads TMEM lanes 32 (w & 3) + lane
-// (its row), column groups of 8 RHS round robin over the four warps of a lane
-// quarter; Re from D_top, Im from D_bot.
-__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, int Rpad, int R, int r0, bool rowok,
-                                            int op, VecRef<float> dst, bool zero) {
+// Epilogue: producer warp w reads TMEM lanes 32 (w & 3) + lane (its row),
+// column groups of 8 RHS round robin over the four warps of a lane quarter;
+// Re from D_top, Im from D_bot.
+__device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, int Rpad, int R, bool rowok, int op,
+                                            VecRef<float> dst, bool zero) {
     constexpr int kQuarterWarps = kTcProducers / 32 / 4;
     const int q = warp & 3;
     for (int c0 = 8 * (warp >> 2); c0 < Rpad; c0 += 8 * kQuarterWarps) {
@@ -308,7 +291,7 @@ __device__ __forceinline__ void tc_epilogue(uint32_t tmem, int warp, int lane, i
                 if (n < R) {
                     const float re = zero ? 0.f : __uint_as_float(v[t]);
                     const float im = zero ? 0.f : __uint_as_float(w[t]);
-                    dst.ptr[(long long)op * dst.ps + (long long)(r0 + n) * dst.rs] = cx<float>{re, im};
+                    dst.ptr[(long long)op * dst.ps + (long long)n * dst.rs] = cx<float>{re, im};
                 }
             }
         }
@@ -321,10 +304,9 @@ __device__ __forceinline__ void tc_setup(TcBars<S>* bars, int tid, int warp) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&bars->full[s], kTcProducers);
             mbar_init(&bars->empty[s], 1);
-            mbar_init(&bars->aload[s], 1);
+            mbar_init(&bars->load[s], 1);
         }
         mbar_init(&bars->done, 1);
-        mbar_init(&bars->tfree, kTcProducers);
         mbar_init(&bars->fin, 1);
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
@@ -338,7 +320,6 @@ __device__ __forceinline__ void tc_setup(TcBars<S>* bars, int tid, int warp) {
     asm volatile("tcgen05.fence::after_thread_sync;");
 }
 
-template <int S>
 __device__ __forceinline__ void tc_teardown(uint32_t tmem, int warp) {
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -346,32 +327,70 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, int warp) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
 }
 
-// The MMA warp's last step: a commit that arrives once every MMA it issued
-// has completed, awaited (bounded) before the tensor memory is released.
-__device__ __forceinline__ void tc_mma_drain(uint64_t* fin, int lane, int* status) {
+// The MMA warp's side of the ring, shared by both kernels.  Chunk g's bulk
+// copies go out S - 1 chunks ahead: into the stage of chunk g - 1 once that
+// chunk's MMAs are done (the MMAs of chunk g are queued behind them, so the
+// tensor pipe stays fed).  Before the MMAs of chunk g it waits for the
+// producers (full) and the copies (load).  Last, a commit that arrives once
+// every MMA has completed is awaited (time-bounded only) before TMEM is
+// released, and so are copies issued but never awaited.
+template <int S, bool REFINE, class Copy>
+__device__ __forceinline__ void tc_mma_loop(TcBars<S>* bars, __nv_bfloat16* ring, size_t stage_elems, uint32_t tmem,
+                                            int nchunk, int Rpad, int lane, int* status, Copy copy) {
+    bool ok = true;
+    int issued = 0;
+    for (; issued < nchunk && issued < S; ++issued) copy(issued);
+    const uint32_t idesc = umma_idesc_bf16(kTcM, Rpad);
+    const uint32_t b_lo = (uint32_t)Rpad * kTcK * 2;
+    for (int c = 0; c < nchunk; ++c) {
+        const int s = c % S;
+        const uint32_t ph = (uint32_t)(c / S) & 1;
+        if (!mbar_wait(&bars->full[s], ph, status) || !mbar_wait(&bars->load[s], ph, status)) {
+            ok = false;
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (lane == 0) {
+            tc_issue_stage<REFINE>(tmem, ring + (size_t)s * stage_elems, idesc, b_lo, c == 0);
+            umma_commit(&bars->empty[s]);
+        }
+        __syncwarp();
+        if (c >= 1 && issued < nchunk && issued == c + S - 1) {
+            if (!mbar_wait(&bars->empty[(c - 1) % S], (uint32_t)((c - 1) / S) & 1, status)) {
+                ok = false;
+                break;
+            }
+            copy(issued);
+            ++issued;
+        }
+    }
+    if (lane == 0) umma_commit(&bars->done);   // arrives at once when no MMA was issued
+    __syncwarp();
+    if (!ok && lane == 0) atomicExch(status, MIDBF_ETIMEOUT);
     if (lane == 0) {
-        umma_commit(fin);
-        if (!mbar_wait(fin, 0, nullptr)) atomicExch(status, MIDBF_ETIMEOUT);
+        umma_commit(&bars->fin);
+        if (!mbar_wait(&bars->fin, 0, nullptr)) atomicExch(status, MIDBF_ETIMEOUT);
+        for (int gg = issued - 1; gg >= 0 && gg >= issued - S; --gg)
+            mbar_wait(&bars->load[gg % S], (uint32_t)(gg / S) & 1, nullptr);
     }
     __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// Middle factor.  One CTA per item (block, 128 role-rows); role rows/cols as
-// in k_s_fly (row_is_row = 1 forward, 0 adjoint with CONJ).
+// Middle factor.  One CTA per item (block, 128 role-rows) and at most kTcR
+// RHS; role rows/cols as in k_s_fly (row_is_row = 1 forward, 0 adjoint with
+// CONJ).  bimg + chunk0[b] * (chunk size) is the block's first B image.
 //
-// Producer iteration for chunk c (ring slot s = g mod S):
-//   wait until the stage's MMAs of chunk g - S are done; threads < 16 stage
-//   the phase data and positions of chunk c + 1 in slot (g + 1) mod S; a
-//   producer barrier; gather the RHS of chunk c + 1 into registers; generate
-//   A_top / A_bot of chunk c; store the RHS of chunk c (gathered one
-//   iteration earlier) as B; arrive on full[s].
-// A slot is rewritten S - 1 iterations after it was last read; S >= 3 and the
-// barrier of every iteration keep that ordered.
+// Producer iteration for chunk c (ring slot s = c mod S): wait until the
+// stage's MMAs of chunk c - S are done; threads < 16 put the phase data of
+// chunk c + 1 (loaded one iteration earlier) into slot (c + 1) mod S and
+// load that of chunk c + 2; a producer barrier; generate A_top / A_bot of
+// chunk c; arrive on full[s].  A slot is rewritten S - 1 iterations after it
+// was last read; S >= 3 and the barrier of every iteration keep that ordered.
 template <int PQ, bool REFINE, bool CONJ>
 __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<float> rs, SSide<float> cs,
-                                                        VecRef<float> src, VecRef<float> dst, int nrhs,
-                                                        int row_is_row, int* status) {
+                                                        const int* chunk0, const __nv_bfloat16* bimg,
+                                                        VecRef<float> dst, int R, int row_is_row, int* status) {
     using Cfg = TcCfg<REFINE>;
     constexpr int S = Cfg::S, NP = Cfg::NP;
     static_assert(S >= 3, "slot reuse needs three ring stages");
@@ -380,7 +399,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);
     TcBars<S>* bars = reinterpret_cast<TcBars<S>*>(tc_smem_raw + S * Cfg::stage_elems * 2);
     __shared__ float scol[S][kTcKc * kTcColStride];
-    __shared__ __align__(16) int spos[S][kTcKc];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 it = st.items[blockIdx.x];
     const int b = it.x;
@@ -391,41 +409,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
     const int P = Sh::fixed ? Sh::P : st.P;
     const int Q = Sh::fixed ? Sh::Q : st.Q;
     const int nchunk = (ncol + kTcKc - 1) / kTcKc;
-    const int npass = (nrhs + kTcR - 1) / kTcR;
+    const int Rpad = (R + 15) & ~15;
+    const size_t bce = tc_bimg_elems(Rpad, REFINE);
+    const __nv_bfloat16* b0 = bimg + (size_t)chunk0[b] * bce;
 
     tc_setup<S>(bars, tid, warp);
     const uint32_t tmem = bars->taddr;
 
     if (warp == kTcProducers / 32) {
-        // ---- MMA warp
-        bool ok = true;
-        int g = 0;
-        for (int p = 0; p < npass && ok; ++p) {
-            const int R = min(kTcR, nrhs - p * kTcR), Rpad = (R + 15) & ~15;
-            const uint32_t idesc = umma_idesc_bf16(kTcM, Rpad);
-            if (p > 0 && !mbar_wait(&bars->tfree, (uint32_t)(p - 1) & 1, status)) {
-                ok = false;
-                break;
+        // ---- MMA warp: B images by bulk copy, MMAs
+        auto copy = [&](int g) {
+            const int s = g % S;
+            if (lane == 0) {
+                mbar_expect_tx(&bars->load[s], (uint32_t)(bce * 2));
+                bulk_g2s(ring + (size_t)s * Cfg::stage_elems + 2 * NP * kTcAElems, b0 + (size_t)g * bce,
+                         (uint32_t)(bce * 2), &bars->load[s]);
             }
-            for (int c = 0; c < nchunk; ++c, ++g) {
-                const int s = g % S;
-                if (!mbar_wait(&bars->full[s], (uint32_t)(g / S) & 1, status)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (lane == 0) {
-                    tc_issue_stage<REFINE>(tmem, ring + (size_t)s * Cfg::stage_elems, idesc, c == 0);
-                    umma_commit(&bars->empty[s]);
-                }
-                __syncwarp();
-            }
-            if (!ok) break;
-            if (lane == 0) umma_commit(&bars->done);
-            __syncwarp();
-        }
-        if (!ok && lane == 0) atomicExch(status, MIDBF_ETIMEOUT);
-        tc_mma_drain(&bars->fin, lane, status);
+        };
+        tc_mma_loop<S, REFINE>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
     } else {
         // ---- producers: thread = (row, quarter of the stage's 16 columns)
         const int ptid = tid;
@@ -442,104 +443,97 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
             for (int q = 0; q < Sh::Q; ++q) rc[q] = q < Q ? rs.c[(size_t)(ro + ii) * Q + q] : 0.f;
         }
         const int op = rok ? rs.pos[ro + i] : 0;
-        // phase data and positions of chunk c into ring slot `slot` (threads < 16)
-        auto stage_cols = [&](int c, int slot) {
-            if (ptid < kTcKc) {
-                const int j = c * kTcKc + ptid;
-                float* cj = scol[slot] + ptid * kTcColStride;
+        // phase data of one column, prefetched into registers by threads < 16
+        float cpre[kTcColStride];
+        auto fetch = [&](int c) {
+            const int j = c * kTcKc + ptid;
+            if (ptid < kTcKc && c < nchunk) {
+#pragma unroll
+                for (int q = 0; q < kTcColStride; ++q) cpre[q] = 0.f;
                 if (j < ncol) {
                     const int e = co + j;
-                    cj[0] = cs.a[e];
-                    for (int q = 0; q < P; ++q) cj[1 + q] = cs.u[(size_t)e * P + q];
-                    for (int q = 0; q < Q; ++q) cj[1 + P + q] = cs.c[(size_t)e * Q + q];
-                    spos[slot][ptid] = cs.pos[e];
-                } else {
-                    spos[slot][ptid] = 0;
+                    cpre[0] = cs.a[e];
+#pragma unroll
+                    for (int q = 0; q < Sh::P; ++q)
+                        if (Sh::fixed || q < P) cpre[1 + q] = cs.u[(size_t)e * P + q];
+#pragma unroll
+                    for (int q = 0; q < Sh::Q; ++q)
+                        if (Sh::fixed || q < Q) cpre[1 + P + q] = cs.c[(size_t)e * Q + q];
                 }
             }
         };
+        auto put = [&](int c) {
+            if (ptid < kTcKc && c < nchunk) {
+                float* cj = scol[c % S] + ptid * kTcColStride;
+#pragma unroll
+                for (int q = 0; q < kTcColStride; ++q) cj[q] = cpre[q];
+            }
+        };
         bool ok = true;
-        int g = 0;
-        for (int p = 0; p < npass && ok; ++p) {
-            const int r0 = p * kTcR;
-            const int R = min(kTcR, nrhs - r0), Rpad = (R + 15) & ~15;
-            TcBItems I;
-            tc_b_items(I, src, r0, R, Rpad, ptid);
-            TcBLoad Lcur, Lnext;
-            if (nchunk > 0) {
-                stage_cols(0, g % S);
-                producers_and(true);
-                tc_load_b(Lcur, I, spos[g % S], ncol, src);
-            }
-            for (int c = 0; c < nchunk; ++c, ++g) {
-                const int s = g % S, s1 = (g + 1) % S;
-                const uint32_t u = (uint32_t)(g / S);
-                // the stage's previous MMAs (chunk g - S) must be done before it is overwritten
-                bool w = true;
-                if (u > 0) w = mbar_wait(&bars->empty[s], (u - 1) & 1, status);
-                const bool more = c + 1 < nchunk;
-                if (more) stage_cols(c + 1, s1);
-                ok = producers_and(w);
-                if (!ok) break;
-                if (more) tc_load_b(Lnext, I, spos[s1], ncol - (c + 1) * kTcKc, src);
-                __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
-                const int j0 = c * kTcKc;
-                // A: this thread's row, columns 4 cq .. 4 cq + 3 = one core row of A_top and of A_bot
-                {
-                    uint32_t th[4], tl[4], bh[4], bl[4];
+        fetch(0);
+        put(0);
+        fetch(1);
+        producers_and(true);
+        for (int c = 0; c < nchunk; ++c) {
+            const int s = c % S;
+            const uint32_t u = (uint32_t)(c / S);
+            // the stage's previous MMAs (chunk c - S) must be done before it is overwritten
+            bool w = true;
+            if (u > 0) w = mbar_wait(&bars->empty[s], (u - 1) & 1, status);
+            put(c + 1);
+            fetch(c + 2);
+            ok = producers_and(w);
+            if (!ok) break;
+            __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
+            const int j0 = c * kTcKc;
+            // this thread's row, columns 4 cq .. 4 cq + 3 = one core row of A_top and of A_bot
+            uint32_t th[4], tl[4], bh[4], bl[4];
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        const int jj = cq * 4 + v;
-                        float er = 0.f, ei = 0.f;
-                        if (rok && j0 + jj < ncol) {
-                            const float* cj = scol[s] + jj * kTcColStride;
-                            float thp = ra + cj[0];
+            for (int v = 0; v < 4; ++v) {
+                const int jj = cq * 4 + v;
+                float er = 0.f, ei = 0.f;
+                if (rok && j0 + jj < ncol) {
+                    const float* cj = scol[s] + jj * kTcColStride;
+                    float thp = ra + cj[0];
 #pragma unroll
-                            for (int q = 0; q < Sh::P; ++q)
-                                if (Sh::fixed || q < P) thp = fmaf(ru[q], cj[1 + q], thp);
-                            if (Sh::Q > 0 && (Sh::fixed || Q > 0)) {
-                                float sq = 0.f;
+                    for (int q = 0; q < Sh::P; ++q)
+                        if (Sh::fixed || q < P) thp = fmaf(ru[q], cj[1 + q], thp);
+                    if (Sh::Q > 0 && (Sh::fixed || Q > 0)) {
+                        float sq = 0.f;
 #pragma unroll
-                                for (int q = 0; q < Sh::Q; ++q)
-                                    if (Sh::fixed || q < Q) sq = fmaf(rc[q], cj[1 + P + q], sq);
-                                thp += sqrtf(sq);
-                            }
-                            thp -= rintf(thp);
-                            sincos2pi(thp, &ei, &er);
-                            if (CONJ) ei = -ei;
-                        }
-                        uint32_t h, l;
-                        split_pair(er, ei, h, l);
-                        th[v] = neg_high(h);
-                        tl[v] = neg_high(l);
-                        bh[v] = swap_halves(h);
-                        bl[v] = swap_halves(l);
+                        for (int q = 0; q < Sh::Q; ++q)
+                            if (Sh::fixed || q < Q) sq = fmaf(rc[q], cj[1 + P + q], sq);
+                        thp += sqrtf(sq);
                     }
-                    const int o = core_off(row, 8 * cq, kTcK);
-                    *reinterpret_cast<uint4*>(stg + o) = make_uint4(th[0], th[1], th[2], th[3]);
-                    *reinterpret_cast<uint4*>(stg + NP * kTcAElems + o) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
-                    if (REFINE) {
-                        *reinterpret_cast<uint4*>(stg + kTcAElems + o) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
-                        *reinterpret_cast<uint4*>(stg + (NP + 1) * kTcAElems + o) =
-                            make_uint4(bl[0], bl[1], bl[2], bl[3]);
-                    }
+                    thp -= rintf(thp);
+                    sincos2pi(thp, &ei, &er);
+                    if (CONJ) ei = -ei;
                 }
-                tc_store_b<REFINE>(Lcur, I, stg + 2 * NP * kTcAElems);
-                asm volatile("fence.proxy.async.shared::cta;");
-                mbar_arrive(&bars->full[s]);
-                if (more) Lcur = Lnext;
+                uint32_t h, l;
+                split_pair(er, ei, h, l);
+                th[v] = neg_high(h);
+                tl[v] = neg_high(l);
+                bh[v] = swap_halves(h);
+                bl[v] = swap_halves(l);
             }
-            if (!ok) break;
-            ok = producers_and(mbar_wait(&bars->done, (uint32_t)p & 1, status));
-            if (!ok) break;
+            const int o = core_off(row, 8 * cq, kTcK);
+            *reinterpret_cast<uint4*>(stg + o) = make_uint4(th[0], th[1], th[2], th[3]);
+            *reinterpret_cast<uint4*>(stg + NP * kTcAElems + o) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+            if (REFINE) {
+                *reinterpret_cast<uint4*>(stg + kTcAElems + o) = make_uint4(tl[0], tl[1], tl[2], tl[3]);
+                *reinterpret_cast<uint4*>(stg + (NP + 1) * kTcAElems + o) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            mbar_arrive(&bars->full[s]);
+        }
+        if (ok) ok = producers_and(mbar_wait(&bars->done, 0, status));
+        if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            tc_epilogue(tmem, warp, lane, Rpad, R, r0, rok, op, dst, nchunk == 0);
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(&bars->tfree);
+            tc_epilogue(tmem, warp, lane, Rpad, R, rok, op, dst, nchunk == 0);
         }
         if (!ok && ptid == 0) atomicExch(status, MIDBF_ETIMEOUT);
     }
-    tc_teardown<S>(tmem, warp);
+    tc_teardown(tmem, warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -552,159 +546,85 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
 // (hi part, then lo part), so one cp.async.bulk moves it; A_bot is derived
 // from it in shared memory.  Two orientations are stored: the block itself
 // (forward) and its conjugate transpose (adjoint).  The item is (block, row
-// tile); the right-hand sides come from the block's input positions.
+// tile); the block's B images start at chunk0.
 struct TcBlock {
     long long img_off;   // element offset (BF16) of the block's first tile image
     int rows, cols;      // complex rows (outputs) and columns (inputs)
-    int in_off, out_off; // offsets into the position arrays
+    int out_off;         // offset into the output positions
+    int chunk0;          // index of the block's first B image
 };
 
 struct TcStage {
     const TcBlock* blocks;
-    const int* in_pos;      // positions of block inputs in the source space
     const int* out_pos;     // positions of block outputs in the destination space
     const __nv_bfloat16* img;
     const int2* items;      // (block, row tile)
 };
 
 template <bool REFINE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, VecRef<float> src, VecRef<float> dst, int nrhs,
-                                                          int* status) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, const __nv_bfloat16* bimg, VecRef<float> dst,
+                                                          int R, int* status) {
     using Cfg = TcCfg<REFINE>;
     constexpr int S = Cfg::S, NP = Cfg::NP;
-    static_assert(S >= 3, "slot reuse needs three ring stages");
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);
     TcBars<S>* bars = reinterpret_cast<TcBars<S>*>(tc_smem_raw + S * Cfg::stage_elems * 2);
-    __shared__ __align__(16) int spos[S][kTcKc];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int2 it = st.items[blockIdx.x];
     const TcBlock bk = st.blocks[it.x];
     const int rt = it.y;
     const int nchunk = (bk.cols + kTcKc - 1) / kTcKc;
-    const int npass = (nrhs + kTcR - 1) / kTcR;
-    const int total = npass * nchunk;
+    const int Rpad = (R + 15) & ~15;
+    const size_t bce = tc_bimg_elems(Rpad, REFINE);
     const __nv_bfloat16* tile0 = st.img + bk.img_off + (size_t)rt * nchunk * NP * kTcTileElems;
-    constexpr uint32_t kCopyBytes = NP * kTcTileElems * 2;
+    const __nv_bfloat16* b0 = bimg + (size_t)bk.chunk0 * bce;
+    constexpr uint32_t kABytes = NP * kTcTileElems * 2;
 
     tc_setup<S>(bars, tid, warp);
     const uint32_t tmem = bars->taddr;
 
     if (warp == kTcProducers / 32) {
-        // ---- MMA warp: bulk copies of the A tiles S - 1 chunks ahead, then the MMAs
-        bool ok = true;
-        int issued = 0;
-        auto copy = [&](int gg) {
-            const int s = gg % S;
+        // ---- MMA warp: A tile and B image of each chunk by bulk copy, MMAs
+        auto copy = [&](int g) {
+            const int s = g % S;
             if (lane == 0) {
-                mbar_expect_tx(&bars->aload[s], kCopyBytes);
-                bulk_g2s(ring + (size_t)s * Cfg::stage_elems, tile0 + (size_t)(gg % nchunk) * NP * kTcTileElems,
-                         kCopyBytes, &bars->aload[s]);
+                __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
+                mbar_expect_tx(&bars->load[s], kABytes + (uint32_t)(bce * 2));
+                bulk_g2s(stg, tile0 + (size_t)g * NP * kTcTileElems, kABytes, &bars->load[s]);
+                bulk_g2s(stg + 2 * NP * kTcAElems, b0 + (size_t)g * bce, (uint32_t)(bce * 2), &bars->load[s]);
             }
         };
-        for (; issued < total && issued < S; ++issued) copy(issued);
-        int g = 0;
-        for (int p = 0; p < npass && ok; ++p) {
-            const int R = min(kTcR, nrhs - p * kTcR), Rpad = (R + 15) & ~15;
-            const uint32_t idesc = umma_idesc_bf16(kTcM, Rpad);
-            if (p > 0 && !mbar_wait(&bars->tfree, (uint32_t)(p - 1) & 1, status)) {
-                ok = false;
-                break;
-            }
-            for (int c = 0; c < nchunk; ++c, ++g) {
-                const int s = g % S;
-                if (!mbar_wait(&bars->full[s], (uint32_t)(g / S) & 1, status)) {
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;");
-                if (lane == 0) {
-                    tc_issue_stage<REFINE>(tmem, ring + (size_t)s * Cfg::stage_elems, idesc, c == 0);
-                    umma_commit(&bars->empty[s]);
-                }
-                __syncwarp();
-                // chunk g + S - 1 takes the stage of chunk g - 1 once its MMAs are done
-                // (the MMAs of chunk g are queued behind them, so the tensor pipe stays fed)
-                if (g >= 1 && issued < total && issued == g + S - 1) {
-                    if (!mbar_wait(&bars->empty[(g - 1) % S], (uint32_t)((g - 1) / S) & 1, status)) {
-                        ok = false;
-                        break;
-                    }
-                    copy(issued);
-                    ++issued;
-                }
-            }
-            if (!ok) break;
-            if (lane == 0) umma_commit(&bars->done);
-            __syncwarp();
-        }
-        if (!ok && lane == 0) atomicExch(status, MIDBF_ETIMEOUT);
-        tc_mma_drain(&bars->fin, lane, status);
-        // copies that no producer waited for (after a timeout) land before the CTA exits
-        if (lane == 0) {
-            for (int gg = issued - 1; gg >= 0 && gg >= issued - S; --gg)
-                mbar_wait(&bars->aload[gg % S], (uint32_t)(gg / S) & 1, nullptr);
-        }
-        __syncwarp();
+        tc_mma_loop<S, REFINE>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
     } else {
-        // ---- producers
+        // ---- producers: A_bot = (Im, Re) from A_top = (Re, -Im), 512 16-byte vectors per part
         const int ptid = tid;
         const int row = ptid & (kTcM - 1);
         const int i = rt * kTcM + row;
         const bool rok = i < bk.rows;
         const int op = rok ? st.out_pos[bk.out_off + i] : 0;
-        auto stage_pos = [&](int c, int slot) {
-            if (ptid < kTcKc) {
-                const int j = c * kTcKc + ptid;
-                spos[slot][ptid] = j < bk.cols ? st.in_pos[bk.in_off + j] : 0;
-            }
-        };
         bool ok = true;
-        int g = 0;
-        for (int p = 0; p < npass && ok; ++p) {
-            const int r0 = p * kTcR;
-            const int R = min(kTcR, nrhs - r0), Rpad = (R + 15) & ~15;
-            TcBItems I;
-            tc_b_items(I, src, r0, R, Rpad, ptid);
-            TcBLoad Lcur, Lnext;
-            if (nchunk > 0) {
-                stage_pos(0, g % S);
-                producers_and(true);
-                tc_load_b(Lcur, I, spos[g % S], bk.cols, src);
-            }
-            for (int c = 0; c < nchunk; ++c, ++g) {
-                const int s = g % S, s1 = (g + 1) % S;
-                const bool more = c + 1 < nchunk;
-                if (more) stage_pos(c + 1, s1);
-                // the stage's A tiles have landed (and its previous MMAs are done: the
-                // copy was issued after them)
-                ok = producers_and(mbar_wait(&bars->aload[s], (uint32_t)(g / S) & 1, status));
-                if (!ok) break;
-                if (more) tc_load_b(Lnext, I, spos[s1], bk.cols - (c + 1) * kTcKc, src);
-                __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
-                // A_bot = (Im, Re) from A_top = (Re, -Im): 512 16-byte vectors per part
+        for (int c = 0; c < nchunk; ++c) {
+            const int s = c % S;
+            ok = producers_and(mbar_wait(&bars->load[s], (uint32_t)(c / S) & 1, status));
+            if (!ok) break;
+            __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
 #pragma unroll
-                for (int part = 0; part < NP; ++part) {
-                    const uint4 a = reinterpret_cast<const uint4*>(stg + part * kTcAElems)[ptid];
-                    reinterpret_cast<uint4*>(stg + (NP + part) * kTcAElems)[ptid] =
-                        make_uint4(top_to_bot(a.x), top_to_bot(a.y), top_to_bot(a.z), top_to_bot(a.w));
-                }
-                tc_store_b<REFINE>(Lcur, I, stg + 2 * NP * kTcAElems);
-                asm volatile("fence.proxy.async.shared::cta;");
-                mbar_arrive(&bars->full[s]);
-                if (more) Lcur = Lnext;
+            for (int part = 0; part < NP; ++part) {
+                const uint4 a = reinterpret_cast<const uint4*>(stg + part * kTcAElems)[ptid];
+                reinterpret_cast<uint4*>(stg + (NP + part) * kTcAElems)[ptid] =
+                    make_uint4(top_to_bot(a.x), top_to_bot(a.y), top_to_bot(a.z), top_to_bot(a.w));
             }
-            if (!ok) break;
-            ok = producers_and(mbar_wait(&bars->done, (uint32_t)p & 1, status));
-            if (!ok) break;
+            asm volatile("fence.proxy.async.shared::cta;");
+            mbar_arrive(&bars->full[s]);
+        }
+        if (ok) ok = producers_and(mbar_wait(&bars->done, 0, status));
+        if (ok) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            tc_epilogue(tmem, warp, lane, Rpad, R, r0, rok, op, dst, nchunk == 0);
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            mbar_arrive(&bars->tfree);
+            tc_epilogue(tmem, warp, lane, Rpad, R, rok, op, dst, nchunk == 0);
         }
         if (!ok && ptid == 0) atomicExch(status, MIDBF_ETIMEOUT);
     }
-    tc_teardown<S>(tmem, warp);
+    tc_teardown(tmem, warp);
 }
 
 }  // namespace midbf_dev

@@ -61,3 +61,16 @@ def test_batched_argument_errors():
     with pytest.raises(mb.MidbfError) as e:
         mb.apply_batched([d32, d64], [x32, x64], [0, 0])
     assert e.value.code == mb.EINVAL
+
+
+def test_batched_launch_count():
+    """midbf_batched_launches: one launch group per level index and kernel
+    variant, so the count lies between the deepest plan's stage count and the
+    sum of all stage counts, and stays the same when instances repeat."""
+    facs = [_fac(16, 16), _fac(32, 16), _fac(32, 64)]
+    dps = [mb.DevicePlan(mb.Plan.load(planio.write(f)), mb.FP32) for f in facs]
+    nst = [len(d.stage_info()) for d in dps]
+    n1 = mb.batched_launches(dps, [0, 1, 0], [1, 3, 20])
+    assert max(nst) <= n1 <= sum(nst)
+    n2 = mb.batched_launches(dps + dps, [0, 1, 0] * 2, [1, 3, 20] * 2)
+    assert n2 == n1
