@@ -199,6 +199,16 @@ void midbf_free(void* p);
  * (cudaMalloc) and synchronizes the device; call before any stream capture.
  * Errors: MIDBF_EINVAL, MIDBF_ENOMEM, MIDBF_ECUDA. */
 int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out);
+
+/* midbf_dplan_create with flags.  MIDBF_DPLAN_CONSUME: release each stage's
+ * ID coefficients from the host plan as soon as they are on the device, so
+ * that host memory falls while the plan is uploaded (plans of ~1e10 entries
+ * do not fit twice).  The plan keeps its structure and statistics, but
+ * midbf_plan_export and further device plans from it then fail with
+ * MIDBF_EINVAL.  Errors as midbf_dplan_create, and MIDBF_EINVAL for unknown
+ * flags or an already consumed plan. */
+#define MIDBF_DPLAN_CONSUME 1
+int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags, midbf_dplan** out);
 void midbf_dplan_destroy(midbf_dplan* dp);
 
 /* Device-side status of a plan's kernels: MIDBF_OK, or MIDBF_ETIMEOUT when a

@@ -86,6 +86,8 @@ midbf_plan_stats = _sig("midbf_plan_stats", C.c_int, [_vp, C.POINTER(midbf_stats
 midbf_plan_destroy = _sig("midbf_plan_destroy", None, [_vp])
 midbf_free = _sig("midbf_free", None, [_vp])
 midbf_dplan_create = _sig("midbf_dplan_create", C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp)])
+midbf_dplan_create_ex = _sig("midbf_dplan_create_ex", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)])
+DPLAN_CONSUME = 1
 midbf_dplan_destroy = _sig("midbf_dplan_destroy", None, [_vp])
 midbf_workspace_size = _sig("midbf_workspace_size", C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)])
 midbf_dplan_bytes = _sig("midbf_dplan_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)])
@@ -281,9 +283,12 @@ class Plan:
 class DevicePlan:
     """Owns a midbf_dplan (plan resident on the current CUDA device)."""
 
-    def __init__(self, plan: Plan, precision=FP32, s_mode=S_ONTHEFLY):
+    def __init__(self, plan: Plan, precision=FP32, s_mode=S_ONTHEFLY, consume=False):
+        """consume=True releases the host plan's coefficients as they are uploaded
+        (midbf_dplan_create_ex with MIDBF_DPLAN_CONSUME)."""
         h = _vp()
-        check(midbf_dplan_create(plan.h, precision, s_mode, C.byref(h)), "midbf_dplan_create")
+        check(midbf_dplan_create_ex(plan.h, precision, s_mode, DPLAN_CONSUME if consume else 0, C.byref(h)),
+              "midbf_dplan_create_ex")
         self.h = h
         self.mode = precision
         self.precision = FP64 if precision == FP64 else FP32   # storage precision of the vectors

@@ -23,6 +23,9 @@
 // alone and sets the starting sample size of the others, so the result does
 // not depend on the thread schedule.
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <atomic>
 #include <functional>
 #include <map>
@@ -335,8 +338,23 @@ struct IdOut {
 
 }  // namespace
 
+// Construction timings on stderr when the environment sets MIDBF_BUILD_LOG.
+struct BuildLog {
+    bool on = std::getenv("MIDBF_BUILD_LOG") != nullptr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), t = t0;
+    void mark(const std::string& what) {
+        if (!on) return;
+        const auto now = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[midbf build %8.2fs +%7.2fs] %s\n",
+                     std::chrono::duration<double>(now - t0).count(), std::chrono::duration<double>(now - t).count(),
+                     what.c_str());
+        t = now;
+    }
+};
+
 std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
     phase_check(ph);
+    BuildLog blog;
     const int d = ph.d, b = 1 << d;
     const int64_t nmax = std::max(ph.nx, ph.nw);
     int L = 0;
@@ -465,7 +483,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
                 for (size_t i = 0; i < pos.size(); ++i) req[q].samples[i] = cand.pts[pos[i]];
             });
             std::vector<IdReply> rep;
-            gpu_id_batch(*gctx, req, prm.tol, prm.kmax, rep);
+            gpu_id_batch(*gctx, req, prm.tol, prm.kmax, rep, prm.store_fp32 != 0);
             for (size_t q = 0; q < which.size(); ++q) {
                 const int64_t e = which[q];
                 const int64_t ncand = (int64_t)cand_fn(e).pts.size();
@@ -479,7 +497,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
                     o.sub.skel = std::move(rep[q].skel);
                     o.sub.red = std::move(rep[q].red);
                     o.sub.T = std::move(rep[q].T);
-                    if (prm.store_fp32) o.sub.to_fp32();
+                    o.sub.Tf = std::move(rep[q].Tf);
                     o.skel_pts.resize(k);
                     for (int64_t i = 0; i < k; ++i) o.skel_pts[i] = colsv[e][o.sub.skel[i]];
                     done[e] = 1;
@@ -507,6 +525,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
         const int nb_w = (int)TW.levels[la].size(), np_x = (int)TX.levels[lq].size();
         nq_of[s] = nq_w;
         np_of[s] = np_x;
+        blog.mark("step " + std::to_string(s) + " start");
         // ---- row IDs (a, Q) ----
         // candidate column sets keyed by (Q, ancestor of a at level lp)
         std::map<std::pair<int, int>, std::unique_ptr<Cand>> ccand;
@@ -547,9 +566,11 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
             }
             return rows;
         };
+        blog.mark("step " + std::to_string(s) + " row candidates");
         run_phase((int64_t)na_x * nq_w, true, (uint64_t)(s * 4 + 1), kest_r, Uf[s],
                   [&](int64_t e) { return rows_of((int)(e / nq_w), (int)(e % nq_w)); },
                   [&](int64_t e) -> const Cand& { return *ccand[keys[e]]; });
+        blog.mark("step " + std::to_string(s) + " row IDs (" + std::to_string((int64_t)na_x * nq_w) + ")");
         ccand.clear();
         // ---- column IDs (beta, P) ----
         std::vector<std::unique_ptr<Cand>> rcand((size_t)np_x * nq_w);
@@ -573,6 +594,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
             }
             return cols;
         };
+        blog.mark("step " + std::to_string(s) + " column candidates");
         run_phase((int64_t)nb_w * np_x, false, (uint64_t)(s * 4 + 2), kest_c, Vf[s],
                   [&](int64_t e) { return cols_of((int)(e / np_x), (int)(e % np_x)); },
                   [&](int64_t e) -> const Cand& {
@@ -581,6 +603,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
                   });
     }
 
+    blog.mark("IDs done");
     // ---- assemble the stages in forward order ----
     // ypos[(ib, ip)] = (offset, k) of y(beta, P_k) in the previous V stage output
     std::vector<std::pair<int64_t, int>> ypos, zpos;
@@ -685,7 +708,9 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
         pl->stages.push_back(std::move(st));
         zpos.swap(znew);
     }
+    blog.mark("stages assembled");
     plan_validate(*pl);
+    blog.mark("validated");
     return pl;
 }
 

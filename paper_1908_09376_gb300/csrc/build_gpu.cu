@@ -377,11 +377,12 @@ std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> gpu_id_context(const Phas
 }
 
 void gpu_id_batch(GpuIdContext& ctx, const std::vector<IdRequest>& reqs, double tol, int kmax,
-                  std::vector<IdReply>& out) {
+                  std::vector<IdReply>& out, bool fp32) {
     using gpuid::Job;
     const size_t nj = reqs.size();
     out.assign(nj, IdReply{});
     if (nj == 0) return;
+    std::vector<cplx> tmp;
     // process in chunks bounded by the matrix pool size (4 GiB of M, same for T)
     const size_t kPool = (size_t)4 << 30;
     size_t j0 = 0;
@@ -437,10 +438,21 @@ void gpu_id_batch(GpuIdContext& ctx, const std::vector<IdRequest>& reqs, double 
             r.k = k;
             r.skel.assign(perm.begin() + (size_t)q * maxn, perm.begin() + (size_t)q * maxn + k);
             r.red.assign(perm.begin() + (size_t)q * maxn + k, perm.begin() + (size_t)q * maxn + n);
-            r.T.resize((size_t)k * (n - k));
-            if (!r.T.empty())
-                CKG(cudaMemcpy(r.T.data(), static_cast<double2*>(ctx.T.p) + jobs[q].t_off, r.T.size() * sizeof(cplx),
-                               cudaMemcpyDeviceToHost));
+            const size_t nt = (size_t)k * (n - k);
+            if (fp32) {
+                // FP32 storage: convert reply by reply, so no phase-wide FP64 copy sits on the host
+                tmp.resize(nt);
+                if (nt)
+                    CKG(cudaMemcpy(tmp.data(), static_cast<double2*>(ctx.T.p) + jobs[q].t_off, nt * sizeof(cplx),
+                                   cudaMemcpyDeviceToHost));
+                r.Tf.resize(nt);
+                for (size_t i = 0; i < nt; ++i) r.Tf[i] = std::complex<float>((float)tmp[i].real(), (float)tmp[i].imag());
+            } else {
+                r.T.resize(nt);
+                if (nt)
+                    CKG(cudaMemcpy(r.T.data(), static_cast<double2*>(ctx.T.p) + jobs[q].t_off, nt * sizeof(cplx),
+                                   cudaMemcpyDeviceToHost));
+            }
         }
         j0 = j1;
     }

@@ -1,0 +1,206 @@
+// Device plans and the launcher interface shared by the translation units of
+// the device library: device.cu (plan upload, the apply, the autotuner, the
+// C ABI) and the kernel launchers launch_rc.cu (interpolation stages, SIMT),
+// launch_s.cu (middle factor, SIMT), launch_tc.cu (tensor cores) and
+// batched.cu (many instances).  Splitting the launchers lets their kernel
+// instantiations compile in parallel.
+#pragma once
+
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <functional>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <set>
+#include <thread>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include "internal.hpp"
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace midbf_gpu {
+
+using namespace midbf;
+using namespace midbf_dev;
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) fail(MIDBF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kRangeC = 64;   // output entries per pattern-C item
+constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory budget per CTA
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t n = 0;
+};
+
+struct DevStageBase {
+    int kind = KIND_V;
+    int64_t in_len = 0, out_len = 0;
+    bool out_user = false, in_user = false;
+};
+
+template <class R>
+struct DevStage : DevStageBase {
+    // ID stages (and stored S)
+    bool id = false;
+    IdStage<R> ids{};
+    IdStage<R> ids1{};   // same data, items for the one-RHS pattern-C kernel
+    int n_items_r = 0, n_items_c = 0, n_items_c1 = 0, rt = 1;
+    int max_nred = 0, max_narrow = 0, max_nsub = 1;
+    // on-the-fly S
+    SStage<R> ss{};
+    SSide<R> srows{}, scols{};
+    const int2* items_rows = nullptr;   // 64-row items (RT = 2)
+    const int2* items_cols = nullptr;
+    const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
+    const int2* items_cols4 = nullptr;
+    int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
+    // tensor-core modes: dense BF16 tile images of the V/U blocks,
+    // [0] forward orientation (stage input -> output), [1] adjoint
+    bool tc = false;
+    TcStage tcs[2]{};
+    int n_tc_items[2] = {0, 0};
+    double tc_bytes[2] = {0, 0};
+    // B-image chunks of the stage input, per orientation (V/U and middle factor)
+    TcPack pk[2]{};
+    const int* chunk0_s[2] = {nullptr, nullptr};   // middle factor: first chunk of each block
+};
+
+}  // namespace midbf_gpu
+
+struct midbf_dplan {
+    int precision = MIDBF_FP32;   // storage: MIDBF_FP32 (also for the BF16 modes) or MIDBF_FP64
+    int tc_mode = 0;              // 0: SIMT only; 1: BF16 tensor cores; 2: BF16 + refinement
+    int* d_status = nullptr;      // device status word written by bounded waits
+    int s_mode = MIDBF_S_ONTHEFLY;
+    int device = 0;
+    int64_t nx = 0, nw = 0;
+    int64_t max_space = 0;        // longest internal vector space
+    size_t factor_bytes = 0, index_bytes = 0;
+    size_t tc_image_bytes = 0;    // dense BF16 tile images (tensor-core modes)
+    int max_tc_chunks = 0;        // most B-image chunks of one tensor-core stage launch
+    std::vector<void*> allocs;
+    std::vector<midbf_gpu::DevStage<float>> st32;
+    std::vector<midbf_gpu::DevStage<double>> st64;
+    // per stage, in forward order: stored bytes streamed once per apply, and
+    // the input + output vector lengths (entries per right-hand side)
+    std::vector<double> stage_fixed_bytes;
+    std::vector<int64_t> stage_vec_entries;
+    std::vector<int> stage_kind;
+    // per stage: complex entries of the method's factor (T entries of the IDs,
+    // or rows x cols of the middle-factor blocks) and of the dense blocks
+    // (identity parts of the IDs included)
+    std::vector<int64_t> stage_entries, stage_dense;
+    // kernel choices per RHS count: [stage][0 forward, 1 adjoint] (midbf_autotune)
+    std::map<int, std::vector<std::array<int, 2>>> tuned;
+    // measurement hooks (midbf_dplan_profile / midbf_stage_times)
+    bool profile = false;
+    mutable std::vector<cudaEvent_t> ev;
+    mutable std::vector<int> ev_stage;   // stage index of each event pair of the last apply
+    mutable int last_nrhs = 1;
+    ~midbf_dplan() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (d_status) cudaFree(d_status);
+        for (void* p : allocs) cudaFree(p);
+    }
+};
+
+namespace midbf_gpu {
+
+// Raise a kernel's dynamic shared-memory limit to the library's cap (device.cu).
+void set_smem_ptr(const void* kernel, size_t bytes);
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+    set_smem_ptr(reinterpret_cast<const void*>(kernel), bytes);
+}
+
+// Right-hand sides per kernel pass: the smallest tile that covers nrhs (at
+// most 16 for FP32, 8 for FP64), halved while the shared-memory need is
+// above the budget.
+template <class R>
+int pick_nr(int nrhs, const std::function<size_t(int)>& smem) {
+    const int cap = sizeof(R) == 4 ? 16 : 8;
+    int nr = 1;
+    while (nr < nrhs && nr < cap) nr *= 2;
+    while (nr > 1 && smem(nr) > kSmemCap) nr /= 2;
+    return nr;
+}
+
+// A forced RHS tile (from the autotuner) is taken when it is one of the
+// compiled tiles and fits the shared-memory budget; otherwise pick_nr decides.
+template <class R>
+int forced_or_pick(int force, int nrhs, const std::function<size_t(int)>& smem) {
+    const int cap = sizeof(R) == 4 ? 16 : 8;
+    if (force > 0 && force <= cap && (force & (force - 1)) == 0 && smem(force) <= kSmemCap) return force;
+    return pick_nr<R>(nrhs, smem);
+}
+
+// Grid of a persistent SIMT launch (device.cu).
+int grid_for(const void* kernel, size_t smem, int nitems, bool persist);
+
+constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
+constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
+
+
+// SIMT RHS tile named by a choice (0: none).
+inline int choice_tile(int choice) {
+    const int base = choice == MIDBF_CHOICE_TENSOR ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
+    return base >= 1 && base <= 16 ? base : 0;
+}
+
+inline bool valid_choice(int choice) {
+    if (choice == MIDBF_CHOICE_TENSOR) return true;
+    const int base = choice & ~MIDBF_CHOICE_PERSIST;
+    return base == MIDBF_CHOICE_DEFAULT || base == MIDBF_CHOICE_COLUMN1 || base == 1 || base == 2 || base == 4 ||
+           base == 8 || base == 16;
+}
+
+// Bytes of the two ping-pong vectors of the workspace, rounded up to 256.
+inline size_t vec_workspace_bytes(const midbf_dplan* dp, int nrhs) {
+    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    return (b + 255) / 256 * 256;
+}
+
+inline size_t tc_bimg_bytes(const midbf_dplan* dp, int nrhs) {
+    if (!dp->tc_mode || dp->max_tc_chunks == 0) return 0;
+    const int Rpad = (std::min(nrhs, kTcR) + 15) & ~15;
+    const size_t b = (size_t)dp->max_tc_chunks * tc_bimg_elems(Rpad, dp->tc_mode == 2) * 2;
+    return (b + 255) / 256 * 256;
+}
+
+// Choice recorded by the autotuner (or midbf_set_choice) for this RHS count,
+// stage and direction; MIDBF_CHOICE_DEFAULT when there is none (device.cu).
+int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint);
+
+// ---- kernel launchers (defined in the launcher units for float and double)
+template <class R>
+void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
+              bool persist = false);
+template <class R>
+void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
+              bool persist = false);
+template <class R>
+void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s,
+              int force = 0, bool persist = false);
+void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint, bool refine,
+               __nv_bfloat16* bimg, int* status, cudaStream_t s);
+void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<float> dst, int nrhs, bool refine,
+                   __nv_bfloat16* bimg, int* status, cudaStream_t s);
+size_t instance_workspace(const midbf_dplan* dp, int nrhs);
+template <class R>
+int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
+                const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, cudaStream_t s,
+                char* ws, bool dry = false);
+
+}  // namespace midbf_gpu

@@ -9,115 +9,17 @@
 //     (or the dense entries, MIDBF_S_STORED).
 // midbf_apply runs the stages in order (forward) or reverse order with
 // conjugated factors (adjoint), ping-ponging between two workspace vectors.
-#include <algorithm>
-#include <cstdio>
-#include <functional>
-#include <mutex>
-#include <array>
-#include <map>
-#include <set>
-#include <type_traits>
-#include <numeric>
-#include <thread>
-#include <tuple>
+#include "dev_plan.cuh"
 
-#include "internal.hpp"
-#include "kernels.cuh"
-#include "tc.cuh"
+#ifdef __GLIBC__
+#include <malloc.h>
+#endif
 
 using namespace midbf;
 using namespace midbf_dev;
+using namespace midbf_gpu;
 
-namespace {
-
-#define CK(call)                                                                                  \
-    do {                                                                                          \
-        cudaError_t e_ = (call);                                                                  \
-        if (e_ != cudaSuccess) fail(MIDBF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-constexpr int kRangeC = 64;   // output entries per pattern-C item
-constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory budget per CTA
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t n = 0;
-};
-
-struct DevStageBase {
-    int kind = KIND_V;
-    int64_t in_len = 0, out_len = 0;
-    bool out_user = false, in_user = false;
-};
-
-template <class R>
-struct DevStage : DevStageBase {
-    // ID stages (and stored S)
-    bool id = false;
-    IdStage<R> ids{};
-    IdStage<R> ids1{};   // same data, items for the one-RHS pattern-C kernel
-    int n_items_r = 0, n_items_c = 0, n_items_c1 = 0, rt = 1;
-    int max_nred = 0, max_narrow = 0, max_nsub = 1;
-    // on-the-fly S
-    SStage<R> ss{};
-    SSide<R> srows{}, scols{};
-    const int2* items_rows = nullptr;   // 64-row items (RT = 2)
-    const int2* items_cols = nullptr;
-    const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
-    const int2* items_cols4 = nullptr;
-    int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
-    // tensor-core modes: dense BF16 tile images of the V/U blocks,
-    // [0] forward orientation (stage input -> output), [1] adjoint
-    bool tc = false;
-    TcStage tcs[2]{};
-    int n_tc_items[2] = {0, 0};
-    double tc_bytes[2] = {0, 0};
-    // B-image chunks of the stage input, per orientation (V/U and middle factor)
-    TcPack pk[2]{};
-    const int* chunk0_s[2] = {nullptr, nullptr};   // middle factor: first chunk of each block
-};
-
-}  // namespace
-
-struct midbf_dplan {
-    int precision = MIDBF_FP32;   // storage: MIDBF_FP32 (also for the BF16 modes) or MIDBF_FP64
-    int tc_mode = 0;              // 0: SIMT only; 1: BF16 tensor cores; 2: BF16 + refinement
-    int* d_status = nullptr;      // device status word written by bounded waits
-    int s_mode = MIDBF_S_ONTHEFLY;
-    int device = 0;
-    int64_t nx = 0, nw = 0;
-    int64_t max_space = 0;        // longest internal vector space
-    size_t factor_bytes = 0, index_bytes = 0;
-    size_t tc_image_bytes = 0;    // dense BF16 tile images (tensor-core modes)
-    int max_tc_chunks = 0;        // most B-image chunks of one tensor-core stage launch
-    std::vector<void*> allocs;
-    std::vector<DevStage<float>> st32;
-    std::vector<DevStage<double>> st64;
-    int launches = 0;
-    // per stage, in forward order: stored bytes streamed once per apply, and
-    // the input + output vector lengths (entries per right-hand side)
-    std::vector<double> stage_fixed_bytes;
-    std::vector<int64_t> stage_vec_entries;
-    std::vector<int> stage_kind;
-    // per stage: complex entries of the method's factor (T entries of the IDs,
-    // or rows x cols of the middle-factor blocks) and of the dense blocks
-    // (identity parts of the IDs included)
-    std::vector<int64_t> stage_entries, stage_dense;
-    // kernel choices per RHS count: [stage][0 forward, 1 adjoint] (midbf_autotune)
-    std::map<int, std::vector<std::array<int, 2>>> tuned;
-    // measurement hooks (midbf_dplan_profile / midbf_stage_times)
-    bool profile = false;
-    mutable std::vector<cudaEvent_t> ev;
-    mutable std::vector<int> ev_stage;   // stage index of each event pair of the last apply
-    mutable int last_nrhs = 1;
-    ~midbf_dplan() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (d_status) cudaFree(d_status);
-        for (void* p : allocs) cudaFree(p);
-    }
-};
-
-namespace {
+namespace midbf_gpu {
 
 template <class T>
 T* upload(midbf_dplan* dp, const std::vector<T>& v, size_t* counter) {
@@ -258,7 +160,43 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     std::vector<int> skel, red, wide_pos, narrow_pos;
     std::vector<ItemR> items_r;
     std::vector<ItemC> items_c, items_c1;
+    // T goes to the device in chunks through a bounded host buffer: the
+    // largest stages hold billions of entries
+    size_t nt = 0;
+    {
+        size_t ns = 0, nk = 0;
+        for (const Block& bk : st.blocks) {
+            if (stored_s) {
+                nt += bk.out_idx.size() * bk.in_idx.size();
+            } else {
+                for (const Sub& sb : bk.subs) {
+                    nt += (size_t)sb.k * (size_t)(sb.m - sb.k);
+                    nk += (size_t)sb.k;
+                    ns += (size_t)(sb.m - sb.k);
+                }
+            }
+        }
+        skel.reserve(nk);
+        red.reserve(ns);
+    }
+    constexpr size_t kChunk = (size_t)64 << 20;   // entries per host-to-device copy
+    cx<R>* dT = nullptr;
+    if (nt) {
+        const size_t bytes = nt * sizeof(cx<R>);
+        if (cudaMalloc(reinterpret_cast<void**>(&dT), bytes) != cudaSuccess)
+            fail(MIDBF_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+        dp->allocs.push_back(dT);
+        dp->factor_bytes += bytes;
+    }
     std::vector<cx<R>> T;
+    T.reserve(std::min(nt, kChunk + 4096));
+    size_t t_done = 0;   // entries already copied to the device
+    auto flush = [&]() {
+        if (T.empty()) return;
+        CK(cudaMemcpy(dT + t_done, T.data(), T.size() * sizeof(cx<R>), cudaMemcpyHostToDevice));
+        t_done += T.size();
+        T.clear();
+    };
     int maxk = 1;
     size_t max_nred = 0, max_narrow = 0, max_nsub = 1;
     const bool is_v = st.kind == KIND_V || st.kind == KIND_S;  // S stored: wide = input like V
@@ -284,7 +222,8 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
             sd.red_off = (int)red.size();
             sd.narrow_off = noff;
             sd.block = (int)b;
-            sd.t_off = (long long)T.size();
+            if (T.size() + (size_t)sd.k * bd.m > kChunk) flush();
+            sd.t_off = (long long)(t_done + T.size());
             for (int j = 0; j < bd.m; ++j) red.push_back(j);
             const size_t base = T.size();
             T.resize(base + (size_t)sd.k * bd.m);
@@ -311,7 +250,8 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
                 sd.red_off = (int)red.size();
                 sd.narrow_off = noff;
                 sd.block = (int)b;
-                sd.t_off = (long long)T.size();
+                if (T.size() + (size_t)sb.k * (sb.m - sb.k) > kChunk) flush();
+                sd.t_off = (long long)(t_done + T.size());
                 noff += sb.k;
                 for (int v : sb.skel) skel.push_back(v);
                 const int nred = sb.m - sb.k;
@@ -355,7 +295,9 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     ds.ids.red = upload(dp, red, &dp->index_bytes);
     ds.ids.wide_pos = upload(dp, wide_pos, &dp->index_bytes);
     ds.ids.narrow_pos = upload(dp, narrow_pos, &dp->index_bytes);
-    ds.ids.T = upload(dp, T, &dp->factor_bytes);
+    flush();
+    if (t_done != nt) fail(MIDBF_EINTERNAL, "coefficient count mismatch");
+    ds.ids.T = dT;
     ds.ids.items_r = upload(dp, items_r, &dp->index_bytes);
     ds.ids.items_c = upload(dp, items_c, &dp->index_bytes);
     ds.ids1 = ds.ids;
@@ -555,8 +497,10 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     }
 }
 
+// consume: the same plan, writable; each stage's ID coefficients are released
+// from it once they are on the device.
 template <class R>
-void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out) {
+void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out, Plan* consume) {
     int64_t in_len = pl.phase.nw;
     for (size_t s = 0; s < pl.stages.size(); ++s) {
         const Stage& st = pl.stages[s];
@@ -572,6 +516,16 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out)
             else make_s_stage<R>(dp, pl, st, ds);
         } else {
             make_id_stage<R>(dp, pl, st, ds, false);
+            if (consume) {
+                for (Block& bk : consume->stages[s].blocks)
+                    for (Sub& sb : bk.subs) {
+                        std::vector<cplx>().swap(sb.T);
+                        std::vector<std::complex<float>>().swap(sb.Tf);
+                    }
+#ifdef __GLIBC__
+                malloc_trim(0);   // hand the freed pages back to the system now
+#endif
+            }
         }
         // algorithmic bytes: factor data and position maps once, vectors per RHS
         // (work-item lists and descriptors are bookkeeping, counted too)
@@ -613,23 +567,6 @@ void set_smem_ptr(const void* kernel, size_t bytes) {
     done.insert({kernel, dev});
 }
 
-template <class K>
-void set_smem(K kernel, size_t bytes) {
-    set_smem_ptr(reinterpret_cast<const void*>(kernel), bytes);
-}
-
-// Right-hand sides per kernel pass: the smallest tile that covers nrhs (at
-// most 16 for FP32, 8 for FP64), halved while the shared-memory need is
-// above the budget.
-template <class R>
-int pick_nr(int nrhs, const std::function<size_t(int)>& smem) {
-    const int cap = sizeof(R) == 4 ? 16 : 8;
-    int nr = 1;
-    while (nr < nrhs && nr < cap) nr *= 2;
-    while (nr > 1 && smem(nr) > kSmemCap) nr /= 2;
-    return nr;
-}
-
 // Grid of a SIMT launch: one CTA per work item, or (persistent) as many CTAs
 // as are resident on the GPU at once, each looping over the items with the
 // grid size as stride (the kernels' item loops).
@@ -654,288 +591,6 @@ int grid_for(const void* kernel, size_t smem, int nitems, bool persist) {
     return std::min(nitems, cap);
 }
 
-template <class R, int RT, int NR, bool CJ>
-void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
-    const size_t sm = pattern_r_smem<R>(ds.max_nred, RT, NR);
-    auto kf = k_pattern_r<R, RT, NR, CJ>;
-    set_smem(kf, sm);
-    const int n = ds.n_items_r;
-    kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
-}
-
-template <class R, int RT, bool CJ>
-void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
-    switch (nr) {
-        case 1: launch_r_t<R, RT, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 2: launch_r_t<R, RT, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 4: launch_r_t<R, RT, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 8: launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
-        default:
-            if constexpr (sizeof(R) == 4) launch_r_t<R, RT, 16, CJ>(ds, src, dst, nrhs, s, persist);
-            else launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist);
-    }
-}
-
-// A forced RHS tile (from the autotuner) is taken when it is one of the
-// compiled tiles and fits the shared-memory budget; otherwise pick_nr decides.
-template <class R>
-int forced_or_pick(int force, int nrhs, const std::function<size_t(int)>& smem) {
-    const int cap = sizeof(R) == 4 ? 16 : 8;
-    if (force > 0 && force <= cap && (force & (force - 1)) == 0 && smem(force) <= kSmemCap) return force;
-    return pick_nr<R>(nrhs, smem);
-}
-
-template <class R>
-void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
-              bool persist = false) {
-    if (ds.n_items_r == 0) return;
-    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_r_smem<R>(ds.max_nred, ds.rt, q); });
-    if (ds.rt == 1) {
-        if (conj) launch_r_nr<R, 1, true>(ds, src, dst, nrhs, nr, s, persist);
-        else launch_r_nr<R, 1, false>(ds, src, dst, nrhs, nr, s, persist);
-    } else {
-        if (conj) launch_r_nr<R, 2, true>(ds, src, dst, nrhs, nr, s, persist);
-        else launch_r_nr<R, 2, false>(ds, src, dst, nrhs, nr, s, persist);
-    }
-    CK(cudaGetLastError());
-}
-
-template <class R, int NR, bool CJ>
-void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
-    const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, NR);
-    auto kf = k_pattern_c<R, NR, CJ>;
-    set_smem(kf, sm);
-    const int n = ds.n_items_c;
-    kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
-}
-
-template <class R, bool CJ>
-void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
-    switch (nr) {
-        case 1: launch_c_t<R, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 2: launch_c_t<R, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 4: launch_c_t<R, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
-        case 8: launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
-        default:
-            if constexpr (sizeof(R) == 4) launch_c_t<R, 16, CJ>(ds, src, dst, nrhs, s, persist);
-            else launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist);
-    }
-}
-
-template <class R>
-void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
-              bool persist = false) {
-    if (ds.n_items_c == 0) return;
-    if (nrhs == 1 && (force == 0 || force == MIDBF_CHOICE_COLUMN1)) {
-        const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
-        if (sm <= kSmemCap) {
-            if (conj) {
-                auto kf = k_pattern_c1<R, true>;
-                set_smem(kf, sm);
-                kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, ds.n_items_c1, persist), kThreads, sm, s>>>(ds.ids1, src, dst, ds.n_items_c1);
-            } else {
-                auto kf = k_pattern_c1<R, false>;
-                set_smem(kf, sm);
-                kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, ds.n_items_c1, persist), kThreads, sm, s>>>(ds.ids1, src, dst, ds.n_items_c1);
-            }
-            CK(cudaGetLastError());
-            return;
-        }
-    }
-    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
-    if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
-    else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
-    CK(cudaGetLastError());
-}
-
-template <class R, int RT, int NR, bool CJ, int PQ>
-void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
-    SStage<R> st = ds.ss;
-    const size_t sm = s_fly_smem<R>(st.P, st.Q, RT, NR);
-    auto kf = k_s_fly<R, RT, NR, CJ, PQ>;
-    set_smem(kf, sm);
-    const bool four = RT == 4;
-    if (!CJ) {
-        st.items = four ? ds.items_rows4 : ds.items_rows;
-        const int n = four ? ds.n_items_rows4 : ds.n_items_rows;
-        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(st, ds.srows, ds.scols, 1, src,
-                                                                                          dst, nrhs, n);
-    } else {
-        st.items = four ? ds.items_cols4 : ds.items_cols;
-        const int n = four ? ds.n_items_cols4 : ds.n_items_cols;
-        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, persist), kThreads, sm, s>>>(st, ds.scols, ds.srows, 0, src,
-                                                                                          dst, nrhs, n);
-    }
-}
-
-// FP32: 128-row items for up to 4 RHS per pass, phase shape fixed at compile
-// time for the workload families.  FP64: the general shape (the plain form
-// stores the middle factor by default).
-template <class R, bool CJ, int PQ>
-void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
-    if constexpr (sizeof(R) == 4) {
-        switch (nr) {
-            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
-            case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
-            case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
-            case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
-            default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s, persist);
-        }
-    } else {
-        switch (nr) {
-            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s, persist);
-        }
-    }
-}
-
-template <class R, bool CJ>
-void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
-    switch (sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0) {
-        case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s, persist); break;
-        case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s, persist); break;
-        case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s, persist); break;
-        case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s, persist); break;
-        case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s, persist); break;
-        default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s, persist);
-    }
-}
-
-template <class R>
-void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s, int force = 0,
-              bool persist = false) {
-    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
-    if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
-    else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
-    CK(cudaGetLastError());
-}
-
-constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
-constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
-
-// Tensor-core stages run in groups of at most kTcR RHS.  Each group first
-// packs the stage input into per-chunk B images (k_pack_b, in the workspace
-// area tc_bimg) and then multiplies.
-inline VecRef<float> rhs_shift(VecRef<float> v, int r0) {
-    v.ptr += (long long)r0 * v.rs;
-    return v;
-}
-
-void launch_pack(const TcPack& pk, VecRef<float> src, int R, bool refine, __nv_bfloat16* bimg, cudaStream_t s) {
-    if (pk.nchunks == 0) return;
-    const int Rpad = (R + 15) & ~15;
-    const int grid = std::min(pk.nchunks, 152 * 8);
-    if (refine) k_pack_b<true><<<grid, 256, 0, s>>>(pk, src, R, Rpad, bimg);
-    else k_pack_b<false><<<grid, 256, 0, s>>>(pk, src, R, Rpad, bimg);
-}
-
-template <int PQ, bool RF, bool CJ>
-void launch_tc_t(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv_bfloat16* bimg, int* status,
-                 cudaStream_t s) {
-    SStage<float> st = ds.ss;
-    const size_t sm = tc_smem_bytes<RF>();
-    auto kf = k_s_tc<PQ, RF, CJ>;
-    set_smem(kf, sm);
-    if (!CJ) {
-        st.items = ds.items_rows4;
-        kf<<<ds.n_items_rows4, kTcThreads, sm, s>>>(st, ds.srows, ds.scols, ds.chunk0_s[0], bimg, dst, R, 1, status);
-    } else {
-        st.items = ds.items_cols4;
-        kf<<<ds.n_items_cols4, kTcThreads, sm, s>>>(st, ds.scols, ds.srows, ds.chunk0_s[1], bimg, dst, R, 0, status);
-    }
-}
-
-template <bool RF, bool CJ>
-void launch_tc_rc(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv_bfloat16* bimg, int* status,
-                  cudaStream_t s) {
-    switch (phase_shape_code(ds.ss.P, ds.ss.Q)) {
-        case 1: launch_tc_t<1, RF, CJ>(ds, dst, R, bimg, status, s); break;
-        case 2: launch_tc_t<2, RF, CJ>(ds, dst, R, bimg, status, s); break;
-        case 3: launch_tc_t<3, RF, CJ>(ds, dst, R, bimg, status, s); break;
-        case 4: launch_tc_t<4, RF, CJ>(ds, dst, R, bimg, status, s); break;
-        case 5: launch_tc_t<5, RF, CJ>(ds, dst, R, bimg, status, s); break;
-        default: launch_tc_t<0, RF, CJ>(ds, dst, R, bimg, status, s);
-    }
-}
-
-// Middle factor on the tensor cores.
-void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint, bool refine,
-               __nv_bfloat16* bimg, int* status, cudaStream_t s) {
-    const int o = adjoint ? 1 : 0;
-    for (int r0 = 0; r0 < nrhs; r0 += kTcR) {
-        const int R = std::min(kTcR, nrhs - r0);
-        launch_pack(ds.pk[o], rhs_shift(src, r0), R, refine, bimg, s);
-        const VecRef<float> d = rhs_shift(dst, r0);
-        if (refine) {
-            if (adjoint) launch_tc_rc<true, true>(ds, d, R, bimg, status, s);
-            else launch_tc_rc<true, false>(ds, d, R, bimg, status, s);
-        } else {
-            if (adjoint) launch_tc_rc<false, true>(ds, d, R, bimg, status, s);
-            else launch_tc_rc<false, false>(ds, d, R, bimg, status, s);
-        }
-    }
-    CK(cudaGetLastError());
-}
-
-// V / U stage on the tensor cores: o = 0 forward, 1 adjoint orientation.
-void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<float> dst, int nrhs, bool refine,
-                   __nv_bfloat16* bimg, int* status, cudaStream_t s) {
-    if (ds.n_tc_items[o] == 0) return;
-    const size_t sm = refine ? tc_smem_bytes<true>() : tc_smem_bytes<false>();
-    for (int r0 = 0; r0 < nrhs; r0 += kTcR) {
-        const int R = std::min(kTcR, nrhs - r0);
-        launch_pack(ds.pk[o], rhs_shift(src, r0), R, refine, bimg, s);
-        const VecRef<float> d = rhs_shift(dst, r0);
-        if (refine) {
-            auto kf = k_blk_tc<true>;
-            set_smem(kf, sm);
-            kf<<<ds.n_tc_items[o], kTcThreads, sm, s>>>(ds.tcs[o], bimg, d, R, status);
-        } else {
-            auto kf = k_blk_tc<false>;
-            set_smem(kf, sm);
-            kf<<<ds.n_tc_items[o], kTcThreads, sm, s>>>(ds.tcs[o], bimg, d, R, status);
-        }
-    }
-    CK(cudaGetLastError());
-}
-
-// Bytes of the B-image area of the workspace for nrhs RHS (0 outside the
-// tensor-core modes): the largest stage's chunks at one group of <= kTcR RHS.
-// Bytes of the two ping-pong vectors of the workspace, rounded up to 256.
-size_t vec_workspace_bytes(const midbf_dplan* dp, int nrhs) {
-    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
-    return (b + 255) / 256 * 256;
-}
-
-size_t tc_bimg_bytes(const midbf_dplan* dp, int nrhs) {
-    if (!dp->tc_mode || dp->max_tc_chunks == 0) return 0;
-    const int Rpad = (std::min(nrhs, kTcR) + 15) & ~15;
-    const size_t b = (size_t)dp->max_tc_chunks * tc_bimg_elems(Rpad, dp->tc_mode == 2) * 2;
-    return (b + 255) / 256 * 256;
-}
-
-template <class R>
-int count_launches(const std::vector<DevStage<R>>& st) {
-    int n = 0;
-    for (auto& s : st) n += 1;
-    return n;
-}
-
-// SIMT RHS tile named by a choice (0: none).
-inline int choice_tile(int choice) {
-    const int base = choice == MIDBF_CHOICE_TENSOR ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
-    return base >= 1 && base <= 16 ? base : 0;
-}
-
-inline bool valid_choice(int choice) {
-    if (choice == MIDBF_CHOICE_TENSOR) return true;
-    const int base = choice & ~MIDBF_CHOICE_PERSIST;
-    return base == MIDBF_CHOICE_DEFAULT || base == MIDBF_CHOICE_COLUMN1 || base == 1 || base == 2 || base == 4 ||
-           base == 8 || base == 16;
-}
 
 // One stage launch.  choice: MIDBF_CHOICE_DEFAULT (the built-in rules: tensor
 // cores in the BF16 modes from kTcMinRhs / kTcBlkMinRhs RHS on, else the SIMT
@@ -968,10 +623,6 @@ void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, Ve
         launch_s<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
     }
 }
-
-// Choice recorded by the autotuner (or midbf_set_choice) for this RHS count,
-// stage and direction; MIDBF_CHOICE_DEFAULT when there is none.
-int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint);
 
 // Run all stages.  user_in/user_out: caller vectors (column-major with ld).
 template <class R>
@@ -1009,226 +660,6 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
     }
 }
 
-
-// ---------------------------------------------------------------------------
-// Batched apply: level index q of every instance in one group of launches.
-// Forward instances run their stage q, adjoint instances their stage ns-1-q;
-// instances are grouped by kernel variant (pattern, rows per lane, RHS tile,
-// phase shape) and up to kBatch instances share a launch.
-template <class R>
-const std::vector<DevStage<R>>& stages_of(const midbf_dplan* dp);
-template <>
-const std::vector<DevStage<float>>& stages_of<float>(const midbf_dplan* dp) { return dp->st32; }
-template <>
-const std::vector<DevStage<double>>& stages_of<double>(const midbf_dplan* dp) { return dp->st64; }
-
-size_t instance_workspace(const midbf_dplan* dp, int nrhs) {
-    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
-    return (b + 255) / 256 * 256;
-}
-
-enum { BT_R = 0, BT_C = 1, BT_C1 = 2, BT_S = 3 };
-
-template <class R, class E>
-void launch_batch_group(const midbf_dplan* const* dps, const std::array<int, 4>& key, const E* ents, int n,
-                        const int* nrhs, const int* adjoint, cudaStream_t s) {
-    const int type = key[0], rt = key[1], nr = key[2], pq = key[3];
-    if (type == BT_S) {
-        BatchS<R> a{};
-        a.ninst = n;
-        size_t sm = 0;
-        int items = 0;
-        for (int k = 0; k < n; ++k) {
-            const E& e = ents[k];
-            const DevStage<R>& ds = stages_of<R>(dps[e.i])[e.sidx];
-            const bool adj = adjoint[e.i] != 0;
-            a.st[k] = ds.ss;
-            const bool four = rt == 4;
-            a.st[k].items = adj ? (four ? ds.items_cols4 : ds.items_cols) : (four ? ds.items_rows4 : ds.items_rows);
-            a.rs[k] = adj ? ds.scols : ds.srows;
-            a.cs[k] = adj ? ds.srows : ds.scols;
-            a.src[k] = e.src;
-            a.dst[k] = e.dst;
-            a.nrhs[k] = nrhs[e.i];
-            a.conj[k] = adj;
-            a.item0[k] = items;
-            items += adj ? (four ? ds.n_items_cols4 : ds.n_items_cols) : (four ? ds.n_items_rows4 : ds.n_items_rows);
-            sm = std::max(sm, s_fly_smem<R>(ds.ss.P, ds.ss.Q, rt, nr));
-        }
-        a.item0[n] = items;
-        if (items == 0) return;
-#define LB(RT_, NR_, PQ_)                                        \
-    {                                                            \
-        auto kf = k_batch_s<R, RT_, NR_, PQ_>;                   \
-        set_smem(kf, sm);                                        \
-        kf<<<items, kThreads, sm, s>>>(a);                       \
-    }
-        if constexpr (sizeof(R) == 4) {
-            auto go = [&](auto pqc) {
-                constexpr int P_ = decltype(pqc)::value;
-                switch (nr) {
-                    case 1: LB(4, 1, P_) break;
-                    case 2: LB(4, 2, P_) break;
-                    case 4: LB(4, 4, P_) break;
-                    case 8: LB(2, 8, P_) break;
-                    default: LB(2, 16, P_)
-                }
-            };
-            switch (pq) {
-                case 1: go(std::integral_constant<int, 1>{}); break;
-                case 2: go(std::integral_constant<int, 2>{}); break;
-                case 3: go(std::integral_constant<int, 3>{}); break;
-                case 4: go(std::integral_constant<int, 4>{}); break;
-                case 5: go(std::integral_constant<int, 5>{}); break;
-                default: go(std::integral_constant<int, 0>{});
-            }
-        } else {
-            switch (nr) {
-                case 1: LB(2, 1, 0) break;
-                case 2: LB(2, 2, 0) break;
-                case 4: LB(2, 4, 0) break;
-                default: LB(2, 8, 0)
-            }
-        }
-#undef LB
-        CK(cudaGetLastError());
-        return;
-    }
-    BatchId<R> a{};
-    a.ninst = n;
-    size_t sm = 0;
-    int items = 0;
-    for (int k = 0; k < n; ++k) {
-        const E& e = ents[k];
-        const DevStage<R>& ds = stages_of<R>(dps[e.i])[e.sidx];
-        a.st[k] = type == BT_C1 ? ds.ids1 : ds.ids;
-        a.src[k] = e.src;
-        a.dst[k] = e.dst;
-        a.nrhs[k] = nrhs[e.i];
-        a.conj[k] = adjoint[e.i] != 0;
-        a.item0[k] = items;
-        if (type == BT_R) {
-            items += ds.n_items_r;
-            sm = std::max(sm, pattern_r_smem<R>(ds.max_nred, rt, nr));
-        } else if (type == BT_C1) {
-            items += ds.n_items_c1;
-            sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1));
-        } else {
-            items += ds.n_items_c;
-            sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, nr));
-        }
-    }
-    a.item0[n] = items;
-    if (items == 0) return;
-#define LK(KF)                                \
-    {                                         \
-        auto kf = KF;                         \
-        set_smem(kf, sm);                     \
-        kf<<<items, kThreads, sm, s>>>(a);    \
-    }
-    if (type == BT_C1) {
-        LK(k_batch_c1<R>)
-    } else if (type == BT_R) {
-        auto go = [&](auto rtc) {
-            constexpr int RT_ = decltype(rtc)::value;
-            switch (nr) {
-                case 1: LK((k_batch_r<R, RT_, 1>)) break;
-                case 2: LK((k_batch_r<R, RT_, 2>)) break;
-                case 4: LK((k_batch_r<R, RT_, 4>)) break;
-                case 8: LK((k_batch_r<R, RT_, 8>)) break;
-                default:
-                    if constexpr (sizeof(R) == 4) LK((k_batch_r<R, RT_, 16>))
-                    else LK((k_batch_r<R, RT_, 8>))
-            }
-        };
-        if (rt == 1) go(std::integral_constant<int, 1>{});
-        else go(std::integral_constant<int, 2>{});
-    } else {
-        switch (nr) {
-            case 1: LK((k_batch_c<R, 1>)) break;
-            case 2: LK((k_batch_c<R, 2>)) break;
-            case 4: LK((k_batch_c<R, 4>)) break;
-            case 8: LK((k_batch_c<R, 8>)) break;
-            default:
-                if constexpr (sizeof(R) == 4) LK((k_batch_c<R, 16>))
-                else LK((k_batch_c<R, 8>))
-        }
-    }
-#undef LK
-    CK(cudaGetLastError());
-}
-
-template <class R>
-// Returns the number of launches; dry = true only counts them.
-int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, const void* const* in,
-                const int64_t* ldin, void* const* out, const int64_t* ldout, const int* nrhs, cudaStream_t s,
-                char* ws, bool dry = false) {
-    int launches = 0;
-    std::vector<cx<R>*> b0(count), b1(count);
-    size_t off = 0;
-    int maxst = 0;
-    for (int i = 0; i < count; ++i) {
-        if (!dry) {
-            b0[i] = reinterpret_cast<cx<R>*>(ws + off);
-            b1[i] = b0[i] + dps[i]->max_space * nrhs[i];
-        }
-        off += instance_workspace(dps[i], nrhs[i]);
-        maxst = std::max(maxst, (int)stages_of<R>(dps[i]).size());
-    }
-    for (int q = 0; q < maxst; ++q) {
-        struct Entry { int i, sidx; VecRef<R> src, dst; };
-        std::map<std::array<int, 4>, std::vector<Entry>> groups;
-        for (int i = 0; i < count; ++i) {
-            const auto& sts = stages_of<R>(dps[i]);
-            const int ns = (int)sts.size();
-            if (q >= ns) continue;
-            const bool adj = adjoint[i] != 0;
-            const int sidx = adj ? ns - 1 - q : q;
-            const DevStage<R>& ds = sts[sidx];
-            const int nr = nrhs[i];
-            VecRef<R> uin{(cx<R>*)in[i], 1, ldin[i]}, uout{(cx<R>*)out[i], 1, ldout[i]};
-            auto internal = [&](int space) { return VecRef<R>{(space & 1) ? b1[i] : b0[i], nr, 1}; };
-            VecRef<R> fin = sidx == 0 ? (adj ? uout : uin) : internal(sidx - 1);
-            VecRef<R> fout = ds.out_user ? (adj ? uin : uout) : internal(sidx);
-            Entry e{i, sidx, adj ? fout : fin, adj ? fin : fout};
-            std::array<int, 4> key{};
-            // a tuned SIMT tile for this instance's RHS count, if any
-            const int force = choice_tile(tuned_choice(dps[i], nr, sidx, adj));
-            if (ds.id) {
-                const bool wide_is_fwd_input = ds.kind != KIND_U;
-                const bool use_r = adj ? !wide_is_fwd_input : wide_is_fwd_input;
-                if (use_r) {
-                    const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
-                    key = {BT_R, ds.rt, t, 0};
-                } else if (nr == 1 && force == 0 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
-                    key = {BT_C1, 0, 1, 0};
-                } else {
-                    const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, qq); });
-                    key = {BT_C, 0, t, 0};
-                }
-            } else {
-                const int t = forced_or_pick<R>(force, nr, [&](int qq) {
-                    return s_fly_smem<R>(ds.ss.P, ds.ss.Q, qq <= 4 && sizeof(R) == 4 ? 4 : 2, qq);
-                });
-                const int rt = (t <= 4 && sizeof(R) == 4) ? 4 : 2;
-                const int pq = sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0;
-                key = {BT_S, rt, t, pq};
-            }
-            groups[key].push_back(e);
-        }
-        for (auto& kv : groups) {
-            const auto& key = kv.first;
-            const auto& ents = kv.second;
-            for (size_t g0 = 0; g0 < ents.size(); g0 += kBatch) {
-                const int n = (int)std::min<size_t>(kBatch, ents.size() - g0);
-                if (!dry) launch_batch_group<R>(dps, key, &ents[g0], n, nrhs, adjoint, s);
-                ++launches;
-            }
-        }
-    }
-    return launches;
-}
 
 int tuned_choice(const midbf_dplan* dp, int nrhs, int sidx, bool adjoint) {
     if (dp->tuned.empty()) return MIDBF_CHOICE_DEFAULT;
@@ -1441,13 +872,21 @@ void midbf_graph_destroy(midbf_graph* graph) { delete graph; }
 
 
 int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_dplan** out) {
+    return midbf_dplan_create_ex(const_cast<midbf_plan*>(plan), precision, s_mode, 0, out);
+}
+
+int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags, midbf_dplan** out) {
     try {
         if (!plan || !out) fail(MIDBF_EINVAL, "null argument");
+        if (flags & ~MIDBF_DPLAN_CONSUME) fail(MIDBF_EINVAL, "unknown flags");
         const int base = precision & ~MIDBF_REFINE;
         if (base != MIDBF_FP64 && base != MIDBF_FP32 && base != MIDBF_BF16) fail(MIDBF_EINVAL, "unknown precision");
         if ((precision & MIDBF_REFINE) && base != MIDBF_BF16) fail(MIDBF_EINVAL, "MIDBF_REFINE applies to MIDBF_BF16");
         if (s_mode != MIDBF_S_ONTHEFLY && s_mode != MIDBF_S_STORED) fail(MIDBF_EINVAL, "unknown middle-factor mode");
-        const Plan& pl = *reinterpret_cast<const Plan*>(plan);
+        Plan& plw = *reinterpret_cast<Plan*>(plan);
+        const Plan& pl = plw;
+        if (pl.released) fail(MIDBF_EINVAL, "the plan's coefficients were released by an earlier consuming upload");
+        Plan* consume = (flags & MIDBF_DPLAN_CONSUME) ? &plw : nullptr;
         int ndev = 0;
         if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) fail(MIDBF_ECUDA, "no CUDA device");
         auto dp = std::make_unique<midbf_dplan>();
@@ -1460,9 +899,9 @@ int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_
         dp->nw = pl.nw();
         if (cudaMalloc(&dp->d_status, sizeof(int)) != cudaSuccess) fail(MIDBF_ENOMEM, "cudaMalloc of the status word failed");
         CK(cudaMemset(dp->d_status, 0, sizeof(int)));
-        if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32);
-        else make_stages<double>(dp.get(), pl, dp->st64);
-        dp->launches = dp->precision == MIDBF_FP32 ? count_launches(dp->st32) : count_launches(dp->st64);
+        if (consume) plw.released = true;   // from here on, whatever happens below
+        if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32, consume);
+        else make_stages<double>(dp.get(), pl, dp->st64, consume);
         CK(cudaDeviceSynchronize());
         *out = dp.release();
         return MIDBF_OK;

@@ -104,6 +104,7 @@ struct Phase {
 };
 
 struct Plan {
+    bool released = false;   // ID coefficients handed to a device plan (midbf_dplan_create_ex)
     int d = 2, L = 0, delta = 1, nsteps = 0;
     double tol = 0.0;
     Phase phase;
@@ -150,10 +151,11 @@ struct IdReply {
     int k = 0;
     std::vector<int32_t> skel, red;
     std::vector<cplx> T;                // k x (n - k) row-major
+    std::vector<std::complex<float>> Tf;   // the same in FP32 (fp32 requested; then T is empty)
 };
 struct GpuIdContext;
 std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> gpu_id_context(const Phase& ph);
 void gpu_id_batch(GpuIdContext& ctx, const std::vector<IdRequest>& reqs, double tol, int kmax,
-                  std::vector<IdReply>& out);
+                  std::vector<IdReply>& out, bool fp32 = false);
 
 }  // namespace midbf

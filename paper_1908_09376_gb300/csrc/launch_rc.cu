@@ -1,0 +1,110 @@
+// Launchers of the interpolation / transfer stages on the SIMT kernels
+// (pattern R: narrow from wide; pattern C: wide from narrow; Sec. 3.2 IDs).
+#include "dev_plan.cuh"
+
+namespace midbf_gpu {
+
+template <class R, int RT, int NR, bool CJ>
+void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
+    const size_t sm = pattern_r_smem<R>(ds.max_nred, RT, NR);
+    const int n = ds.n_items_r;
+    if (persist) {
+        auto kf = k_pattern_r_p<R, RT, NR, CJ>;
+        set_smem(kf, sm);
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
+    } else {
+        auto kf = k_pattern_r<R, RT, NR, CJ>;
+        set_smem(kf, sm);
+        kf<<<n, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+    }
+}
+
+template <class R, int RT, bool CJ>
+void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
+    switch (nr) {
+        case 1: launch_r_t<R, RT, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 2: launch_r_t<R, RT, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 4: launch_r_t<R, RT, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 8: launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
+        default:
+            if constexpr (sizeof(R) == 4) launch_r_t<R, RT, 16, CJ>(ds, src, dst, nrhs, s, persist);
+            else launch_r_t<R, RT, 8, CJ>(ds, src, dst, nrhs, s, persist);
+    }
+}
+
+template <class R>
+void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force,
+              bool persist) {
+    if (ds.n_items_r == 0) return;
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_r_smem<R>(ds.max_nred, ds.rt, q); });
+    if (ds.rt == 1) {
+        if (conj) launch_r_nr<R, 1, true>(ds, src, dst, nrhs, nr, s, persist);
+        else launch_r_nr<R, 1, false>(ds, src, dst, nrhs, nr, s, persist);
+    } else {
+        if (conj) launch_r_nr<R, 2, true>(ds, src, dst, nrhs, nr, s, persist);
+        else launch_r_nr<R, 2, false>(ds, src, dst, nrhs, nr, s, persist);
+    }
+    CK(cudaGetLastError());
+}
+
+template <class R, int NR, bool CJ>
+void launch_c_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
+    const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, NR);
+    const int n = ds.n_items_c;
+    if (persist) {
+        auto kf = k_pattern_c_p<R, NR, CJ>;
+        set_smem(kf, sm);
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
+    } else {
+        auto kf = k_pattern_c<R, NR, CJ>;
+        set_smem(kf, sm);
+        kf<<<n, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+    }
+}
+
+template <class R, bool CJ>
+void launch_c_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
+    switch (nr) {
+        case 1: launch_c_t<R, 1, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 2: launch_c_t<R, 2, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 4: launch_c_t<R, 4, CJ>(ds, src, dst, nrhs, s, persist); break;
+        case 8: launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist); break;
+        default:
+            if constexpr (sizeof(R) == 4) launch_c_t<R, 16, CJ>(ds, src, dst, nrhs, s, persist);
+            else launch_c_t<R, 8, CJ>(ds, src, dst, nrhs, s, persist);
+    }
+}
+
+template <class R>
+void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force,
+              bool persist) {
+    if (ds.n_items_c == 0) return;
+    if (nrhs == 1 && (force == 0 || force == MIDBF_CHOICE_COLUMN1)) {
+        const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
+        if (sm <= kSmemCap) {
+            const int n = ds.n_items_c1;
+            if (persist) {
+                auto kf = conj ? k_pattern_c1_p<R, true> : k_pattern_c1_p<R, false>;
+                set_smem(kf, sm);
+                kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(ds.ids1, src, dst, n);
+            } else {
+                auto kf = conj ? k_pattern_c1<R, true> : k_pattern_c1<R, false>;
+                set_smem(kf, sm);
+                kf<<<n, kThreads, sm, s>>>(ds.ids1, src, dst);
+            }
+            CK(cudaGetLastError());
+            return;
+        }
+    }
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, q); });
+    if (conj) launch_c_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
+    else launch_c_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
+    CK(cudaGetLastError());
+}
+
+template void launch_r<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
+template void launch_r<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
+template void launch_c<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
+template void launch_c<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
+
+}  // namespace midbf_gpu

@@ -1,0 +1,74 @@
+// Launchers of the middle factor made on the fly on the SIMT kernels (Sec. 3.5).
+#include "dev_plan.cuh"
+
+namespace midbf_gpu {
+
+template <class R, int RT, int NR, bool CJ, int PQ>
+void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, cudaStream_t s, bool persist) {
+    SStage<R> st = ds.ss;
+    const size_t sm = s_fly_smem<R>(st.P, st.Q, RT, NR);
+    const bool four = RT == 4;
+    st.items = !CJ ? (four ? ds.items_rows4 : ds.items_rows) : (four ? ds.items_cols4 : ds.items_cols);
+    const int n = !CJ ? (four ? ds.n_items_rows4 : ds.n_items_rows) : (four ? ds.n_items_cols4 : ds.n_items_cols);
+    const SSide<R>& rside = !CJ ? ds.srows : ds.scols;
+    const SSide<R>& cside = !CJ ? ds.scols : ds.srows;
+    if (persist) {
+        auto kf = k_s_fly_p<R, RT, NR, CJ, PQ>;
+        set_smem(kf, sm);
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(st, rside, cside, !CJ ? 1 : 0,
+                                                                                       src, dst, nrhs, n);
+    } else {
+        auto kf = k_s_fly<R, RT, NR, CJ, PQ>;
+        set_smem(kf, sm);
+        kf<<<n, kThreads, sm, s>>>(st, rside, cside, !CJ ? 1 : 0, src, dst, nrhs);
+    }
+}
+
+// FP32: 128-row items for up to 4 RHS per pass, phase shape fixed at compile
+// time for the workload families.  FP64: the general shape (the plain form
+// stores the middle factor by default).
+template <class R, bool CJ, int PQ>
+void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
+    if constexpr (sizeof(R) == 4) {
+        switch (nr) {
+            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s, persist);
+        }
+    } else {
+        switch (nr) {
+            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
+            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s, persist);
+        }
+    }
+}
+
+template <class R, bool CJ>
+void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
+    switch (sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0) {
+        case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s, persist); break;
+        case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s, persist); break;
+        default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s, persist);
+    }
+}
+
+template <class R>
+void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s, int force,
+              bool persist) {
+    const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
+    if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
+    else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);
+    CK(cudaGetLastError());
+}
+
+template void launch_s<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
+template void launch_s<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
+
+}  // namespace midbf_gpu

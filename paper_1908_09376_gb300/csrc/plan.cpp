@@ -54,6 +54,7 @@ const char kMagic[8] = {'M', 'I', 'D', 'B', 'F', 'P', 'L', '1'};
 }  // namespace
 
 std::vector<uint8_t> plan_serialize(const Plan& pl) {
+    if (pl.released) fail(MIDBF_EINVAL, "the plan's coefficients were released by a consuming upload");
     Writer w;
     for (char c : kMagic) w.put(c);
     w.put<int32_t>(pl.d);
@@ -254,7 +255,7 @@ void plan_stats(const Plan& pl, midbf_stats* st) {
             }
             for (const Sub& sb : b.subs) {
                 st->nsubs++;
-                st->t_entries += (int64_t)sb.t_size();
+                st->t_entries += (int64_t)sb.k * (int64_t)(sb.m - sb.k);
                 st->skel_entries += sb.k;
                 st->max_rank = std::max(st->max_rank, (int)sb.k);
                 ranks += sb.k;

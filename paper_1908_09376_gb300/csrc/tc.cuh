@@ -30,6 +30,8 @@
 
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace midbf_dev {
@@ -59,6 +61,23 @@ template <bool REFINE>
 __host__ __device__ constexpr size_t tc_smem_bytes() {
     return TcCfg<REFINE>::smem;
 }
+
+// Small-RHS ring of k_blk_tc (Rpad <= kTcRSmall): a stage holds A_top, B and
+// B2 = (Im Y, -Re Y) instead of A_top and A_bot, since D_bot = A_top B2^T as
+// well; with small B parts that is half the bytes, so twice the stages (and
+// twice the A-tile bytes in flight).
+constexpr int kTcRSmall = 64;
+
+template <bool REFINE>
+struct TcCfgSmall {
+    static constexpr int NP = REFINE ? 2 : 1;
+    static constexpr int S = REFINE ? 6 : 8;
+    static constexpr size_t b_elems = (size_t)kTcRSmall * kTcK;   // one B part
+    // one stage: A_top[NP], B[NP], B2[NP]
+    static constexpr size_t stage_elems = (size_t)NP * (kTcAElems + 2 * b_elems);
+    static constexpr size_t bar_bytes = 256;
+    static constexpr size_t smem = (size_t)S * stage_elems * 2 + bar_bytes;
+};
 
 // Offset (elements) of (row r, k) in the K-major core-matrix layout with K columns.
 __host__ __device__ __forceinline__ int core_off(int r, int k, int K) {
@@ -227,6 +246,37 @@ __device__ __forceinline__ void tc_issue_stage(uint32_t tmem, const __nv_bfloat1
     }
 }
 
+// MMAs of one small-RHS stage: D_top += A_top B^T, D_bot += A_top B2^T.
+template <bool REFINE>
+__device__ __forceinline__ void tc_issue_stage_b2(uint32_t tmem, const __nv_bfloat16* stage, uint32_t idesc,
+                                                  uint32_t b_lo, bool first) {
+    using Cfg = TcCfgSmall<REFINE>;
+    constexpr int NP = Cfg::NP;
+    constexpr uint32_t sbo = (kTcK / 8) * 128;
+    const uint32_t aT = smem_u32(stage);
+    const uint32_t bB = aT + NP * kTcAElems * 2;
+    const uint32_t b2B = bB + (uint32_t)(NP * Cfg::b_elems * 2);
+#pragma unroll
+    for (int kk = 0; kk < kTcK; kk += 16) {
+        const uint32_t ko = (uint32_t)(kk / 8) * 128;
+        const uint32_t acc = (first && kk == 0) ? 0u : 1u;
+        const uint64_t th = umma_desc(aT + ko, 128, sbo);
+        const uint64_t bh = umma_desc(bB + ko, 128, sbo);
+        const uint64_t ch = umma_desc(b2B + ko, 128, sbo);
+        umma_bf16(tmem, th, bh, idesc, acc);
+        umma_bf16(tmem + kTcR, th, ch, idesc, acc);
+        if (REFINE) {
+            const uint64_t tl = umma_desc(aT + kTcAElems * 2 + ko, 128, sbo);
+            const uint64_t bl = umma_desc(bB + b_lo + ko, 128, sbo);
+            const uint64_t cl = umma_desc(b2B + b_lo + ko, 128, sbo);
+            umma_bf16(tmem, th, bl, idesc, 1u);
+            umma_bf16(tmem, tl, bh, idesc, 1u);
+            umma_bf16(tmem + kTcR, th, cl, idesc, 1u);
+            umma_bf16(tmem + kTcR, tl, ch, idesc, 1u);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Right-hand sides.  Before a tensor-core stage runs, k_pack_b gathers its
 // input once per (block, 16-column chunk) and writes the chunk's B image:
@@ -334,7 +384,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, int warp) {
 // producers (full) and the copies (load).  Last, a commit that arrives once
 // every MMA has completed is awaited (time-bounded only) before TMEM is
 // released, and so are copies issued but never awaited.
-template <int S, bool REFINE, class Copy>
+template <int S, bool REFINE, bool B2, class Copy>
 __device__ __forceinline__ void tc_mma_loop(TcBars<S>* bars, __nv_bfloat16* ring, size_t stage_elems, uint32_t tmem,
                                             int nchunk, int Rpad, int lane, int* status, Copy copy) {
     bool ok = true;
@@ -351,7 +401,8 @@ __device__ __forceinline__ void tc_mma_loop(TcBars<S>* bars, __nv_bfloat16* ring
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (lane == 0) {
-            tc_issue_stage<REFINE>(tmem, ring + (size_t)s * stage_elems, idesc, b_lo, c == 0);
+            if (B2) tc_issue_stage_b2<REFINE>(tmem, ring + (size_t)s * stage_elems, idesc, b_lo, c == 0);
+            else tc_issue_stage<REFINE>(tmem, ring + (size_t)s * stage_elems, idesc, b_lo, c == 0);
             umma_commit(&bars->empty[s]);
         }
         __syncwarp();
@@ -426,7 +477,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
                          (uint32_t)(bce * 2), &bars->load[s]);
             }
         };
-        tc_mma_loop<S, REFINE>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
+        tc_mma_loop<S, REFINE, false>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
     } else {
         // ---- producers: thread = (row, quarter of the stage's 16 columns)
         const int ptid = tid;
@@ -561,10 +612,12 @@ struct TcStage {
     const int2* items;      // (block, row tile)
 };
 
-template <bool REFINE>
+// SMALL (Rpad <= kTcRSmall): the TcCfgSmall ring; producers derive B2 from B.
+// Otherwise the TcCfg ring; producers derive A_bot from A_top.
+template <bool REFINE, bool SMALL>
 __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, const __nv_bfloat16* bimg, VecRef<float> dst,
                                                           int R, int* status) {
-    using Cfg = TcCfg<REFINE>;
+    using Cfg = typename std::conditional<SMALL, TcCfgSmall<REFINE>, TcCfg<REFINE>>::type;
     constexpr int S = Cfg::S, NP = Cfg::NP;
     extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
     __nv_bfloat16* ring = reinterpret_cast<__nv_bfloat16*>(tc_smem_raw);
@@ -585,16 +638,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, const __nv
 
     if (warp == kTcProducers / 32) {
         // ---- MMA warp: A tile and B image of each chunk by bulk copy, MMAs
+        // offset of the B region in a stage: after A_top and A_bot, or (SMALL) after A_top
+        constexpr size_t b_at = (SMALL ? 1 : 2) * (size_t)NP * kTcAElems;
         auto copy = [&](int g) {
             const int s = g % S;
             if (lane == 0) {
                 __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
                 mbar_expect_tx(&bars->load[s], kABytes + (uint32_t)(bce * 2));
                 bulk_g2s(stg, tile0 + (size_t)g * NP * kTcTileElems, kABytes, &bars->load[s]);
-                bulk_g2s(stg + 2 * NP * kTcAElems, b0 + (size_t)g * bce, (uint32_t)(bce * 2), &bars->load[s]);
+                bulk_g2s(stg + b_at, b0 + (size_t)g * bce, (uint32_t)(bce * 2), &bars->load[s]);
             }
         };
-        tc_mma_loop<S, REFINE>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
+        tc_mma_loop<S, REFINE, SMALL>(bars, ring, Cfg::stage_elems, tmem, nchunk, Rpad, lane, status, copy);
     } else {
         // ---- producers: A_bot = (Im, Re) from A_top = (Re, -Im), 512 16-byte vectors per part
         const int ptid = tid;
@@ -608,11 +663,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, const __nv
             ok = producers_and(mbar_wait(&bars->load[s], (uint32_t)(c / S) & 1, status));
             if (!ok) break;
             __nv_bfloat16* stg = ring + (size_t)s * Cfg::stage_elems;
+            if constexpr (SMALL) {
+                // B2 = (Im Y, -Re Y) word by word from B = (Re Y, Im Y), hi and lo parts
+                const uint4* b = reinterpret_cast<const uint4*>(stg + NP * kTcAElems);
+                uint4* b2 = reinterpret_cast<uint4*>(stg + NP * kTcAElems + NP * Cfg::b_elems);
+                const int nv = (int)(bce / 8);   // 16-byte vectors of the B image
+                for (int v = ptid; v < nv; v += kTcProducers) {
+                    const uint4 w = b[v];
+                    b2[v] = make_uint4(neg_high(swap_halves(w.x)), neg_high(swap_halves(w.y)),
+                                       neg_high(swap_halves(w.z)), neg_high(swap_halves(w.w)));
+                }
+            } else {
 #pragma unroll
-            for (int part = 0; part < NP; ++part) {
-                const uint4 a = reinterpret_cast<const uint4*>(stg + part * kTcAElems)[ptid];
-                reinterpret_cast<uint4*>(stg + (NP + part) * kTcAElems)[ptid] =
-                    make_uint4(top_to_bot(a.x), top_to_bot(a.y), top_to_bot(a.z), top_to_bot(a.w));
+                for (int part = 0; part < NP; ++part) {
+                    const uint4 a = reinterpret_cast<const uint4*>(stg + part * kTcAElems)[ptid];
+                    reinterpret_cast<uint4*>(stg + (NP + part) * kTcAElems)[ptid] =
+                        make_uint4(top_to_bot(a.x), top_to_bot(a.y), top_to_bot(a.z), top_to_bot(a.w));
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;");
             mbar_arrive(&bars->full[s]);

@@ -57,3 +57,43 @@ def test_device_build_3d_and_lowrank():
     fac = planio.read(plan.export())
     f = synth.complex_gaussian(1024, 1, 3)[:, 0]
     assert direct.rel_l2(midbf.apply(fac, f), direct.direct_sum(fac.phase, f)) < 2e-5
+
+
+def test_device_build_fp32_storage():
+    """device_ids with store_fp32: the replies are converted to FP32 one by one;
+    the plan has the device build's structure and its coefficients rounded to
+    FP32."""
+    X, W, bx, bw = _grid(64)
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    p64 = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, device_ids=1)
+    p32 = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, device_ids=1, store_fp32=1)
+    assert p32.stats() == p64.stats()
+    f64, f32 = planio.read(p64.export()), planio.read(p32.export())
+    for s64, s32 in zip(f64.stages, f32.stages):
+        for b64, b32 in zip(s64.blocks, s32.blocks):
+            for u64, u32 in zip(b64.subs, b32.subs):
+                assert np.array_equal(u64.skel, u32.skel)
+                assert np.array_equal(u32.T, u64.T.astype(np.complex64).astype(np.complex128))
+
+
+def test_consuming_upload():
+    """MIDBF_DPLAN_CONSUME: the device plan equals the one from an ordinary
+    upload bit for bit; the consumed host plan keeps its statistics but
+    refuses export and further uploads."""
+    X, W, bx, bw = _grid(64)
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    keep = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, store_fp32=1)
+    used = mb.Plan.build(ph, tol=1e-6, n0=64, boxX=bx, boxW=bw, store_fp32=1)
+    st = used.stats()
+    d1 = mb.DevicePlan(keep, mb.FP32)
+    d2 = mb.DevicePlan(used, mb.FP32, consume=True)
+    assert used.stats() == st
+    F = torch.from_numpy(synth.complex_gaussian(64 * 64, 3, 7).T.copy()).to("cuda", torch.complex64)
+    assert torch.equal(d1.apply(F), d2.apply(F))
+    assert torch.equal(d1.apply(F, adjoint=True), d2.apply(F, adjoint=True))
+    with pytest.raises(mb.MidbfError) as e:
+        used.export()
+    assert e.value.code == mb.EINVAL
+    with pytest.raises(mb.MidbfError) as e:
+        mb.DevicePlan(used, mb.FP32)
+    assert e.value.code == mb.EINVAL
