@@ -593,6 +593,20 @@ def main():
         if tc_active:
             row["TFLOPs"] = round(stage_flops(k[0], k[1]) / (ms_ * 1e-3) / 1e12, 1)
         stage_rows.append(row)
+    # the middle factor made on the fly with the SIMT kernels is bound by the SFU: every
+    # entry needs one sine and one cosine, 16 SFU operations per clock per SM
+    sfu_peak = 152 * 16 * 2.07e9 / 2 / 1e9          # G entries/s at the maximum SM clock
+    s_entries_of = {q_: sinfo[q_][1] for q_ in range(ns) if sinfo[q_][0] == 1}
+
+    def hbm_roofline(exclude_s):
+        rows = [(k, v) for k, v in stage_ms.items() if not (exclude_s and k[2] == 1)]
+        (d_, q_, kind_, by_), t_ = max(rows, key=lambda kv: statistics.mean(kv[1]))
+        ms_ = statistics.mean(t_)
+        a_ = by_ / (ms_ * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(a_, 1), "peak": peak, "unit": "GB/s", "frac": round(a_ / peak, 4),
+                "traffic": None, "kernel": f"{d_} stage {q_} ({'VSU'[kind_]})", "peak_source": peak_kind}
+
+    roofline_hbm = None
     if tc_active:
         achieved = stage_flops(direction, q) / (dom_ms * 1e-3) / 1e12
         issued = achieved * (3 if mode_name == "bf16r" else 1)
@@ -601,6 +615,15 @@ def main():
                     "kernel": f"{direction} stage {q} ({'VSU'[kind]})", "peak_source": PEAK_BF16_SOURCE,
                     "issued_TFLOPs": round(issued, 1), "issued_frac": round(issued / PEAK_BF16, 4),
                     "flops": "8 per complex multiply-add of the factor entries per RHS; refinement issues 3x"}
+    elif kind == 1:
+        sidx = q if direction == "fwd" else ns - 1 - q
+        achieved = s_entries_of[sidx] / (dom_ms * 1e-3) / 1e9
+        roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(sfu_peak, 1), "unit": "Gentries/s",
+                    "frac": round(achieved / sfu_peak, 4), "traffic": None,
+                    "kernel": f"{direction} stage {q} (S, made on the fly)",
+                    "peak_source": "derived: 152 SMs x 16 SFU ops/clk x 2.07 GHz / 2 (one sine, one cosine per entry)"}
+        roofline_hbm = hbm_roofline(True)
+        roofline_hbm["whole_step_GBps"] = round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1)
     else:
         achieved = by / (dom_ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -682,6 +705,8 @@ def main():
         dptc = mb.DevicePlan(plan, mb.BF16 | mb.REFINE, mb.S_ONTHEFLY)
         Gt = torch.empty((R, N), dtype=torch.complex64, device=dev)
         Ht = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        del wsR
+        wsR = torch.empty(dptc.workspace_bytes(R), dtype=torch.uint8, device=dev)   # with the RHS-image area
         dptc.apply(F, out=Gt, workspace=wsR)
         torch.cuda.synchronize()
         totT = 0.0
@@ -752,7 +777,8 @@ def main():
                       "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": f"replicas x{ws}", "build_s": round(t_build, 1),
                       "upload_s": round(t_up, 1)},
-           "roofline": roofline, "stages": stage_rows, "rel_l2_direct_sampled": acc, "clocks": clk, "e2e": e2e,
+           "roofline": roofline, "roofline_hbm": roofline_hbm, "stages": stage_rows, "rel_l2_direct_sampled": acc,
+           "clocks": clk, "e2e": e2e,
            "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
     out.update(extras)
     if rank == 0:
