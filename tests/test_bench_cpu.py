@@ -1,0 +1,56 @@
+"""bench.py's accuracy report (no GPU): the sampled direct-sum error is at
+rounding level for exact outputs and reports a planted perturbation at its
+size, in both directions; the workload defaults follow the configurations."""
+import sys
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct
+from oracle.phase import Phase as OPhase
+
+mb = pytest.importorskip("paper_1908_09376_gb300")
+
+
+def _bench():
+    sys.argv = ["bench.py"]
+    import bench
+    return bench
+
+
+def test_sampled_direct_error_exact_and_perturbed():
+    bench = _bench()
+    n = 16
+    X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    oph = OPhase(synth.PHASE_FIO2D, X, W)
+    F = synth.complex_gaussian(n * n, 3, 0)
+    Hin = synth.complex_gaussian(n * n, 3, 1)
+    G = np.stack([direct.direct_sum(oph, F[:, r]) for r in range(3)], 1)
+    H = np.stack([direct.direct_adjoint(oph, Hin[:, r]) for r in range(3)], 1)
+    rows = synth.sample_rows(n * n, 20, 3)
+    cols = synth.sample_rows(n * n, 20, 4)
+    ef, ea = bench.sampled_direct_error(ph, F.T, G.T, Hin.T, H.T, rows, cols)
+    assert ef < 1e-13 and ea < 1e-13
+    rng = np.random.default_rng(0)
+    Gp = G * (1 + 1e-3 * rng.standard_normal(G.shape))
+    Hp = H * (1 + 1e-3 * rng.standard_normal(H.shape))
+    ef, ea = bench.sampled_direct_error(ph, F.T, Gp.T, Hin.T, Hp.T, rows, cols)
+    assert 3e-4 < ef < 3e-3 and 3e-4 < ea < 3e-3
+    assert bench.sampled_direct_error(ph, F.T, G.T, Hin.T, H.T, rows, cols[:0])[1] is None
+
+
+def test_workload_defaults():
+    bench = _bench()
+
+    class A:
+        workload, n, nrhs, mode, build, store, tune, graph = "fio2d", None, None, None, None, None, None, None
+    w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
+    assert (w.n, nrhs, mode, build, store, tune, graph) == (256, 1, "fp32", "host", "fp64", False, False)
+    A.workload = "fio3d_n32"
+    w, nrhs, mode, *_ = bench.pick_workload(A)
+    assert (w.d, w.N, nrhs, mode) == (3, 32768, 256, "bf16r")
+    A.workload = "fio2d_jump"
+    w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
+    assert (w.N, nrhs, mode, store, tune, graph) == (1024 * 1024, 16, "fp32", "fp32", True, True)

@@ -64,3 +64,28 @@ def test_fullsize_many_rhs_matches_single(plan):
         a1 = dp.apply(G[r].contiguous(), adjoint=True)
         assert (torch.linalg.vector_norm(G[r] - g1) / torch.linalg.vector_norm(g1)).item() < 1e-6
         assert (torch.linalg.vector_norm(A[r] - a1) / torch.linalg.vector_norm(a1)).item() < 1e-6
+
+
+def test_fullsize_tensor_cores_64_rhs(plan):
+    """The tensor-core form (BF16 with the hi/lo refinement products) at the
+    benchmark's size with 64 RHS: every column within 5e-5 of the FP32 apply of
+    the same factors, and sampled rows of three columns within 1e-4 of the
+    oracle's direct sum (the mixed-form bound)."""
+    pl, oph = plan
+    N = N_GRID ** 2
+    R = 64
+    F = synth.complex_gaussian(N, R, 9)
+    Ft = torch.from_numpy(F.T.copy()).to("cuda", torch.complex64)
+    d32 = mb.DevicePlan(pl, mb.FP32)
+    dtc = mb.DevicePlan(pl, mb.BF16 | mb.REFINE)
+    for adj in (False, True):
+        g32 = d32.apply(Ft, adjoint=adj)
+        gtc = dtc.apply(Ft, adjoint=adj)
+        rel = (torch.linalg.vector_norm(gtc - g32) / torch.linalg.vector_norm(g32)).item()
+        assert rel < 5e-5, (adj, rel)
+    assert dtc.status() == mb.OK
+    G = dtc.apply(Ft).cpu().numpy()
+    rows = synth.sample_rows(N, 64, 3)
+    for r in (0, 31, 63):
+        e = direct.rel_l2(G[r][rows], direct.direct_sum(oph, F[:, r], rows=rows))
+        assert e < 1e-4, (r, e)
