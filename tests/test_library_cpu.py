@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol():
         assert n in mb.EXPORTED, f"binding lacks {n}"
 
 
+def test_binding_constants_match_header():
+    """Every MIDBF_* value the header defines equals the binding's constant of
+    the same name (status codes, phase families, precisions, middle-factor
+    modes, kernel choices, device-plan flags), and the phase ids match synth."""
+    txt = open(os.path.join(ROOT, "include", "midbf.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define MIDBF_([A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt)}
+    assert len(defs) >= 25
+    for name, val in defs.items():
+        assert getattr(mb, name) == val, name
+    for fam in ("FIO2D", "FIO3D", "FIO2D_JUMP", "DOT", "ZERO", "SEPARABLE", "LOWRANK"):
+        assert getattr(synth, "PHASE_" + fam) == defs["PHASE_" + fam]
+
+
 def _grid(n):
     X = synth.uniform_grid(n, 2)
     W = synth.frequency_grid(n, 2)
