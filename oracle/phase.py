@@ -9,6 +9,8 @@
 * FIO2D_JUMP: FIO2D + 0.5 |xi| sign(x1 - 0.5), sign(0) := +1; piecewise smooth
   with one discontinuity (the paper's setting of eq. (1) allows O(1) of them).
 * DOT: x.xi (the Fourier kernel of Example 2, Sec. 4).
+* DISTANCE: |x - xi|_2.  Example 3 (Sec. 4) uses h |x - xi| on a sphere mesh;
+  the workloads pass the points scaled by h, which gives the same Phi.
 * ZERO, SEPARABLE: K of rank one; used as pins.
 * LOWRANK: Psi(i, j) = sum_t U[i,t] V[j,t], the output form of Algorithm 7.
 
@@ -55,6 +57,8 @@ def coordinate_phase(family: int, x: np.ndarray, w: np.ndarray) -> np.ndarray:
         return dot
     if family == synth.PHASE_ZERO:
         return np.zeros(np.broadcast_shapes(x.shape[:-1], w.shape[:-1]))
+    if family == synth.PHASE_DISTANCE:
+        return np.sqrt(np.sum((x - w) ** 2, axis=-1))
     if family == synth.PHASE_SEPARABLE:
         return np.sum(np.sin(twopi * x), axis=-1) + 0.05 * np.sum(w * w, axis=-1)
     if family in (synth.PHASE_FIO2D, synth.PHASE_FIO2D_JUMP):

@@ -1,0 +1,155 @@
+"""Examples 2 and 3 of Sec. 4 on the host (no GPU).
+
+Example 2: the 3D non-uniform Fourier transform, Phi = x.xi with X and Omega
+N = n^3 random points in [0,1)^3.  Example 3: the Helmholtz phase h |x - xi|
+on the two halves of a triangular sphere mesh (an icosahedron refined
+uniformly, new nodes projected onto the sphere), h = sqrt(N)/10.
+
+This file pins the oracle side: the mesh against its closed-form counts
+(Euler's formula, the regular icosahedron), the distance phase against exact
+distances on the sphere, the direct sum against a closed form, the oracle's
+construction against the dense kernel, and its recovery (Algorithms 4-5)
+against the values Table 3 prints.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import direct, midbf, recovery
+from oracle.phase import Phase as OPhase
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _edges(faces):
+    e = np.concatenate([faces[:, [0, 1]], faces[:, [1, 2]], faces[:, [2, 0]]])
+    e.sort(axis=1)
+    return np.unique(e, axis=0)
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_icosphere_counts_and_euler(level):
+    v, f = synth.icosphere(level)
+    E = _edges(f)
+    assert len(v) == 10 * 4 ** level + 2 and len(f) == 20 * 4 ** level and len(E) == 30 * 4 ** level
+    assert len(v) - len(E) + len(f) == 2                       # a closed surface of genus 0
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0, atol=1e-15)
+    # every edge is shared by exactly two triangles (a closed manifold mesh)
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    e.sort(axis=1)
+    _, cnt = np.unique(e, axis=0, return_counts=True)
+    assert np.all(cnt == 2)
+    # uniform refinement: edge lengths within a factor 1.3 of each other
+    ln = np.linalg.norm(v[E[:, 0]] - v[E[:, 1]], axis=1)
+    assert ln.max() / ln.min() < 1.3
+
+
+def test_icosahedron_is_regular():
+    v, f = synth.icosphere(0)
+    E = _edges(f)
+    ln = np.linalg.norm(v[E[:, 0]] - v[E[:, 1]], axis=1)
+    # edge of the regular icosahedron of circumradius 1: 4 / sqrt(10 + 2 sqrt 5)
+    assert np.allclose(ln, 4.0 / math.sqrt(10.0 + 2.0 * math.sqrt(5.0)), rtol=1e-14)
+    assert np.all(np.bincount(E.ravel(), minlength=12) == 5)
+    # faces are the 20 equilateral triangles, no two alike
+    assert len({tuple(sorted(t)) for t in f.tolist()}) == 20
+
+
+def test_hemispheres_partition_the_mesh():
+    v, _ = synth.icosphere(3)
+    X, W = synth.hemispheres(v)
+    assert len(X) + len(W) == len(v)
+    assert np.all(X[:, 2] >= 0) and np.all(W[:, 2] < 0)
+    allp = {tuple(p) for p in v.tolist()}
+    assert {tuple(p) for p in X.tolist()} | {tuple(p) for p in W.tolist()} == allp
+    w = synth.WORKLOADS["helmholtz_l5"]
+    assert w.nx == len(synth.hemispheres(synth.icosphere(5)[0])[0]) and abs(w.h - math.sqrt(w.nx) / 10) < 1e-15
+
+
+def test_distance_phase_exact_values():
+    """|x - xi| on the sphere scaled by h: 0 on coincident points, 2h between
+    antipodes, h sqrt(2) between orthogonal points, symmetric, and obeying the
+    triangle inequality."""
+    h = 7.5
+    P = OPhase(synth.PHASE_DISTANCE, h * np.array([[0, 0, 1.0], [1.0, 0, 0], [0, 0.6, 0.8]]),
+               h * np.array([[0, 0, -1.0], [0, 0, 1.0], [0, 1.0, 0]]))
+    assert P(0, 0) == pytest.approx(2 * h, rel=1e-15)
+    assert P(0, 1) == 0.0
+    assert P(1, 2) == pytest.approx(h * math.sqrt(2.0), rel=1e-15)
+    assert P(2, 1) == pytest.approx(h * math.sqrt(0.6 ** 2 + 0.2 ** 2), rel=1e-15)
+    rng = np.random.default_rng(5)
+    a, b, c = rng.standard_normal((3, 200, 3))
+    Q = OPhase(synth.PHASE_DISTANCE, np.concatenate([a, b]), np.concatenate([b, c]))
+    ab, bc, ac = Q(np.arange(200), np.arange(200)), Q(200 + np.arange(200), 200 + np.arange(200)), \
+        Q(np.arange(200), 200 + np.arange(200))
+    assert np.all(ac <= ab + bc + 1e-12)
+    Qt = OPhase(synth.PHASE_DISTANCE, np.concatenate([b, c]), np.concatenate([a, b]))
+    assert np.array_equal(Qt(np.arange(200), np.arange(200)), ab)
+
+
+def test_direct_sum_of_a_point_source_at_the_centre():
+    """One source at the centre of the sphere: every receiver on the sphere
+    of radius h sees exp(2 pi i h) f."""
+    w = synth.WORKLOADS["helmholtz_l5"]
+    X, _, _, _ = w.points()
+    P = OPhase(synth.PHASE_DISTANCE, X, np.zeros((1, 3)))
+    g = direct.direct_sum(P, np.array([0.5 - 0.25j]))
+    assert np.allclose(g, np.exp(2j * np.pi * w.h) * (0.5 - 0.25j), rtol=0, atol=1e-12)
+
+
+def test_oracle_construction_on_the_sphere():
+    """The oracle's MIDBF over the non-uniform (surface) octrees of a small
+    sphere mesh reproduces the dense kernel (Sec. 3.6 tolerance, t = 5)."""
+    v, _ = synth.icosphere(3)
+    X0, W0 = synth.hemispheres(v)
+    h = math.sqrt(len(X0)) / 10
+    P = OPhase(synth.PHASE_DISTANCE, h * X0, h * W0)
+    box = (np.full(3, -h), 2 * h)
+    fac = midbf.build(P, n0=8, tol=1e-8, t=5.0, boxX=box, boxW=box)
+    assert fac.L >= 2
+    K = direct.dense_kernel(P)
+    D = midbf.dense(fac)
+    assert np.linalg.norm(D - K) / np.linalg.norm(K) < 1e-6
+
+
+def _table3():
+    rows = []
+    for line in open(os.path.join(GOLD, "table3_tau_disc.txt")):
+        if line.strip() and not line.startswith("#"):
+            n, tau, dr, dc = line.split()
+            rows.append((int(n), float(Fraction(tau)), float(dr), float(dc)))
+    return rows
+
+
+def _oracle_detections(n, tau, nvec=8):
+    """Average numbers of detected discontinuities over nvec recovered rows
+    (along the Omega path) and columns (along the X path), Algorithms 4 and 5."""
+    N = n ** 3
+    X = synth.uniform_random_points(N, 3, 0)
+    W = synth.uniform_random_points(N, 3, 1)
+    P = OPhase(synth.PHASE_DOT, X, W)
+    PX, PW = recovery.recovery_path(X), recovery.recovery_path(W)
+    idx = np.concatenate([[0], synth.sample_rows(N, nvec, 11)[:nvec - 1]])
+    dr, dc = [], []
+    for i in idx:
+        u = P(np.full(N, i), np.arange(N))
+        dr.append(len(recovery.recovery_vector(u - np.floor(u), tau, PW)[1]) - 1)
+        u = P(np.arange(N), np.full(N, i))
+        dc.append(len(recovery.recovery_vector(u - np.floor(u), tau, PX)[1]) - 1)
+    return float(np.mean(dr)), float(np.mean(dc))
+
+
+def test_tau_study_of_table3():
+    """Table 3: no discontinuity is detected at tau = 1/4 for any n, and the
+    counts grow as tau shrinks and fall as n grows (averages over 8 recovered
+    rows and columns, Algorithms 4 and 5)."""
+    for n, tau, dr, dc in _table3():
+        if dr == 0 and dc == 0 and n <= 16:
+            assert _oracle_detections(n, tau) == (0.0, 0.0), (n, tau)
+    counts = [_oracle_detections(8, t)[0] for t in (1 / 4, 1 / 6, 1 / 8, 1 / 10)]
+    assert counts == sorted(counts) and counts[-1] > 0
+    assert _oracle_detections(16, 1 / 10)[0] < counts[-1]
