@@ -6,13 +6,17 @@ on the n = 256 grid, N = 65,536 points, phase x.xi + sqrt(c1^2 xi1^2 +
 c2^2 xi2^2), ID tolerance 1e-6, n0 = 64 (L = 5).  --workload selects the 3D
 variant (N = 32,768 random points, 256 RHS, BF16 tensor cores with the
 refinement products) or the 2D phase with a jump across x1 = 1/2 on the
-n = 1024 grid (16 RHS).  Synthetic inputs (synth.py), seeded.
+n = 1024 grid (16 RHS), Example 2 (3D non-uniform Fourier transform, x.xi over
+n^3 random points in the unit cube on both sides) or Example 3 (Helmholtz
+phase h |x - xi| on the two halves of a sphere mesh of 10 4^l + 2 nodes).
+Synthetic inputs (synth.py), seeded.
 
 A step is one pass of the whole hot path over one batch: the forward apply
 g = K f followed by the adjoint apply K^H g, both through all levels (V
 levels, the on-the-fly middle factor, U levels), in the mixed form (complex
 FP32, or BF16 tensor cores with FP32 accumulation).  value = points*RHS
-processed per second over all ranks (2 N R per step per rank).  Extra keys
+processed per second over all ranks ((|X| + |Omega|) R per step per rank:
+the forward apply produces |X| outputs per RHS, the adjoint |Omega|).  Extra keys
 report the rel-L2 error of the step's outputs against FP64 direct sums on
 sampled rows, the plain FP64 form, 64 right-hand sides, the roofline of the
 dominant kernel, the end-to-end time through the host-buffer C entry point,
@@ -52,9 +56,12 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="grid size of the 2D workloads")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
-    ap.add_argument("--workload", default="fio2d", choices=["fio2d", "fio3d_n32", "fio2d_jump", "batched"],
+    ap.add_argument("--workload", default="fio2d",
+                    choices=["fio2d", "fio3d_n32", "fio2d_jump", "batched", "nuft3d", "helmholtz"],
                     help="fio2d: 2D FIO phase on the n x n grid (--n, default 256); fio3d_n32: 3D, N = 32,768, "
-                         "random X; fio2d_jump: 2D with the jump |xi| sign(x1 - 1/2) (--n, default 1024)")
+                         "random X; fio2d_jump: 2D with the jump |xi| sign(x1 - 1/2) (--n, default 1024); "
+                         "nuft3d: Example 2, N = n^3 random points (--n, default 64); helmholtz: Example 3 on "
+                         "the sphere mesh of refinement level --n (default 6: 20,609 x 20,353 points)")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's)")
     ap.add_argument("--mode", default=None, choices=["fp32", "bf16", "bf16r"],
                     help="arithmetic: complex FP32, or BF16 tensor cores with FP32 accumulation "
@@ -112,10 +119,21 @@ def pick_workload(args):
         n = args.n or base.n
         w = synth.Workload(f"fio2d_jump_n{n}", 2, n, base.phase, base.tol, base.n0, base.nrhs, base.f_seed,
                            sample_rows=base.sample_rows, sample_seed=base.sample_seed)
+    elif args.workload == "nuft3d":
+        base = synth.WORKLOADS["nuft3d_n64"]
+        n = args.n or base.n
+        w = synth.Workload(f"nuft3d_n{n}", 3, n, base.phase, base.tol, base.n0, 1, base.f_seed,
+                           x_kind="random", x_seed=base.x_seed, w_kind="random", w_seed=base.w_seed,
+                           sample_rows=256, sample_seed=3)
+    elif args.workload == "helmholtz":
+        base = synth.WORKLOADS["helmholtz_l6"]
+        lev = args.n or base.n
+        w = synth.Workload(f"helmholtz_l{lev}", 3, lev, base.phase, base.tol, base.n0, 1, base.f_seed,
+                           x_kind="sphere", w_kind="sphere", sample_rows=256, sample_seed=3, t=base.t)
     else:
         w = synth.WORKLOADS[args.workload]
     nrhs = args.nrhs if args.nrhs is not None else w.nrhs
-    mode = args.mode if args.mode is not None else ("bf16r" if w.d == 3 else "fp32")
+    mode = args.mode if args.mode is not None else ("bf16r" if w.phase == synth.PHASE_FIO3D else "fp32")
     build = args.build if args.build is not None else ("host" if args.workload == "fio2d" else "device")
     store = args.store if args.store is not None else ("fp32" if args.workload == "fio2d_jump" else "fp64")
     jump = args.workload == "fio2d_jump"
@@ -125,7 +143,8 @@ def pick_workload(args):
 
 
 PHASE_NAMES = {synth.PHASE_FIO2D: "FIO2D closed form", synth.PHASE_FIO3D: "FIO3D closed form",
-               synth.PHASE_FIO2D_JUMP: "FIO2D + jump closed form"}
+               synth.PHASE_FIO2D_JUMP: "FIO2D + jump closed form", synth.PHASE_DOT: "x.xi closed form",
+               synth.PHASE_DISTANCE: "h |x - xi| closed form (h folded into the points)"}
 
 
 def sampled_direct_error(ph, F, G, Hin, H, rows, cols, chunk=16):
@@ -478,11 +497,12 @@ def main():
     wl, R1, mode_name, build_site, store, tune, use_graph = pick_workload(args)
     n = wl.n
     N = wl.N
+    nx, nw = wl.nx, wl.nw
     X, W, bx, bw = wl.points()
 
     t0 = time.perf_counter()
     ph = mb.Phase.closed_form(wl.phase, X, W)
-    plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads,
+    plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads, t=wl.t,
                          device_ids=1 if build_site == "device" else 0, store_fp32=1 if store == "fp32" else 0)
     t_build = time.perf_counter() - t0
     st = plan.stats()
@@ -499,10 +519,10 @@ def main():
     fbytes, ibytes = dp32.bytes()
     sinfo = dp32.stage_info()
 
-    f_host = synth.complex_gaussian(N, R1, wl.f_seed)
+    f_host = synth.complex_gaussian(nw, R1, wl.f_seed)
     f = torch.from_numpy(f_host.T.copy()).to(dev, torch.complex64)
-    g = torch.empty((R1, N), dtype=torch.complex64, device=dev)
-    h = torch.empty((R1, N), dtype=torch.complex64, device=dev)
+    g = torch.empty((R1, nx), dtype=torch.complex64, device=dev)
+    h = torch.empty((R1, nw), dtype=torch.complex64, device=dev)
     if R1 == 1:
         f, g, h = f[0], g[0], h[0]
     ws1 = torch.empty(dp32.workspace_bytes(R1), dtype=torch.uint8, device=dev)
@@ -555,7 +575,8 @@ def main():
         pg.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     clk = clocks.stop()
-    ms_per_step, value = aggregate(sum(step_ms), 2 * N * R1, args.steps, pg, dev)
+    units = (nx + nw) * R1                  # outputs of the forward and the adjoint apply
+    ms_per_step, value = aggregate(sum(step_ms), units, args.steps, pg, dev)
 
     # the same steps again with CUDA events around every stage launch
     dp32.profile(True)
@@ -637,10 +658,10 @@ def main():
     acc = None
     if rank == 0 and wl.sample_rows:
         torch.cuda.synchronize()
-        Gn = g.reshape(R1, N).cpu().numpy()
-        Hn = h.reshape(R1, N).cpu().numpy()
-        rows = synth.sample_rows(N, wl.sample_rows, wl.sample_seed)
-        cols = synth.sample_rows(N, wl.sample_rows, wl.sample_seed + 1)
+        Gn = g.reshape(R1, nx).cpu().numpy()
+        Hn = h.reshape(R1, nw).cpu().numpy()
+        rows = synth.sample_rows(nx, wl.sample_rows, wl.sample_seed)
+        cols = synth.sample_rows(nw, wl.sample_rows, wl.sample_seed + 1)
         e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Gn, Hn, rows, cols)
         acc = {"forward": e_f, "adjoint": e_a, "rows": int(wl.sample_rows),
                "reference": "FP64 direct sum over all columns (rows) for sampled outputs"}
@@ -738,8 +759,8 @@ def main():
 
     # end to end through the host-buffer entry point (pinned host memory)
     fh = torch.from_numpy(f_host.T.astype(np.complex64).copy()).pin_memory()
-    gh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
-    hh = torch.empty((R1, N), dtype=torch.complex64).pin_memory()
+    gh = torch.empty((R1, nx), dtype=torch.complex64).pin_memory()
+    hh = torch.empty((R1, nw), dtype=torch.complex64).pin_memory()
     wsh = torch.empty(dp32.workspace_bytes(R1, host_io=True), dtype=torch.uint8, device=dev)
     for _ in range(3):
         mb.check(mb.midbf_apply_host(dp32.h, 0, fh.data_ptr(), gh.data_ptr(), R1, stream.cuda_stream,
@@ -753,8 +774,8 @@ def main():
         mb.check(mb.midbf_apply_host(dp32.h, 1, gh.data_ptr(), hh.data_ptr(), R1, stream.cuda_stream,
                                      wsh.data_ptr(), wsh.numel()), "apply_host")
     e2e_s = (time.perf_counter() - te) / ke
-    e2e = {"value": ws * 2 * N * R1 / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": 2 * N * R1 * 8,
-           "d2h_bytes_per_step": 2 * N * R1 * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
+    e2e = {"value": ws * units / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": (nw + nx) * R1 * 8,
+           "d2h_bytes_per_step": (nx + nw) * R1 * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_extras and R1 == 1 and args.workload == "fio2d":
@@ -766,7 +787,8 @@ def main():
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-           "config": {"workload": wl.name, "N": N, "d": wl.d, "phase": PHASE_NAMES.get(wl.phase, str(wl.phase)),
+           "config": {"workload": wl.name, "N": N, "nx": nx, "nw": nw, "d": wl.d,
+                      "phase": PHASE_NAMES.get(wl.phase, str(wl.phase)),
                       "points": wl.x_kind, "nrhs": R1, "mode": mode_name, "step": "forward + adjoint apply",
                       "tol": wl.tol, "n0": wl.n0, "L": st["L"], "build": build_site, "store": store,
                       "autotuned": tune, "tune_s": round(t_tune, 1), "cuda_graph": use_graph,

@@ -57,6 +57,8 @@ extern "C" {
 #define MIDBF_PHASE_ZERO        5 /* 0 (rank-one K)                                */
 #define MIDBF_PHASE_SEPARABLE   6 /* sum_k sin(2 pi x_k) + 0.05 sum_k xi_k^2        */
 #define MIDBF_PHASE_LOWRANK     7 /* Psi(i, j) = sum_t U[i,t] V[j,t] (Algorithm 7)  */
+#define MIDBF_PHASE_DISTANCE    8 /* |x - xi|_2: the Helmholtz phase h |x - xi| of
+                                     Sec. 4 Example 3 with h folded into the points */
 
 /* ---- apply precisions -------------------------------------------------- */
 #define MIDBF_FP64  0   /* plain form: complex128 data and arithmetic          */
@@ -84,7 +86,8 @@ const char* midbf_version(void);
 /* ---- phases -------------------------------------------------------------
  * midbf_phase_closed_form: Phi of one of the MIDBF_PHASE_* closed forms over
  * the point sets X (nx x d) and W (nw x d), d = 2 or 3.  FIO2D/FIO2D_JUMP need
- * d = 2, FIO3D needs d = 3.  Errors: MIDBF_EINVAL.
+ * d = 2, FIO3D needs d = 3.  For h |x - xi| pass h X and h W with DISTANCE.
+ * Errors: MIDBF_EINVAL.
  */
 int midbf_phase_closed_form(int family, int d, int64_t nx, const double* X,
                             int64_t nw, const double* W, midbf_phase** out);

@@ -74,7 +74,15 @@ void launch_batch_group(const midbf_dplan* const* dps, const std::array<int, 4>&
                 case 3: go(std::integral_constant<int, 3>{}); break;
                 case 4: go(std::integral_constant<int, 4>{}); break;
                 case 5: go(std::integral_constant<int, 5>{}); break;
+                case kShapeDistance: go(std::integral_constant<int, kShapeDistance>{}); break;
                 default: go(std::integral_constant<int, 0>{});
+            }
+        } else if (pq == kShapeDistance) {
+            switch (nr) {
+                case 1: LB(2, 1, kShapeDistance) break;
+                case 2: LB(2, 2, kShapeDistance) break;
+                case 4: LB(2, 4, kShapeDistance) break;
+                default: LB(2, 8, kShapeDistance)
             }
         } else {
             switch (nr) {
@@ -205,7 +213,7 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
                     return s_fly_smem<R>(ds.ss.P, ds.ss.Q, qq <= 4 && sizeof(R) == 4 ? 4 : 2, qq);
                 });
                 const int rt = (t <= 4 && sizeof(R) == 4) ? 4 : 2;
-                const int pq = sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0;
+                const int pq = s_shape(ds);
                 key = {BT_S, rt, t, pq};
             }
             groups[key].push_back(e);

@@ -75,7 +75,12 @@ __device__ double phase_eval(const PhaseDev& ph, long long i, long long j) {
             }
             return dot + sqrt(acc);
         }
-        default: return 0.0;
+        case MIDBF_PHASE_DISTANCE: {
+            double s = 0.0;
+            for (int k = 0; k < ph.d; ++k) s += (x[k] - w[k]) * (x[k] - w[k]);
+            return sqrt(s);
+        }
+        default: return 0.0;   // unreachable: gpu_id_context admits the families above only
     }
 }
 
@@ -359,6 +364,12 @@ struct GpuIdContext {
 std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> gpu_id_context(const Phase& ph) {
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) fail(MIDBF_ECUDA, "no CUDA device for the device build");
+    switch (ph.family) {
+        case MIDBF_PHASE_LOWRANK: case MIDBF_PHASE_DOT: case MIDBF_PHASE_ZERO: case MIDBF_PHASE_SEPARABLE:
+        case MIDBF_PHASE_FIO2D: case MIDBF_PHASE_FIO2D_JUMP: case MIDBF_PHASE_FIO3D: case MIDBF_PHASE_DISTANCE:
+            break;
+        default: fail(MIDBF_EINVAL, "phase family without a device evaluation");
+    }
     std::unique_ptr<GpuIdContext, void (*)(GpuIdContext*)> c(new GpuIdContext, [](GpuIdContext* p) { delete p; });
     auto up = [](gpuid::DevMem& m, const std::vector<double>& v) -> const double* {
         if (v.empty()) return nullptr;

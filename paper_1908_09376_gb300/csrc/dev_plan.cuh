@@ -64,6 +64,7 @@ struct DevStage : DevStageBase {
     const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
     const int2* items_cols4 = nullptr;
     int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
+    bool s_dist = false;                // square-root term in the distance form (DISTANCE phase)
     // tensor-core modes: dense BF16 tile images of the V/U blocks,
     // [0] forward orientation (stage input -> output), [1] adjoint
     bool tc = false;
@@ -74,6 +75,15 @@ struct DevStage : DevStageBase {
     TcPack pk[2]{};
     const int* chunk0_s[2] = {nullptr, nullptr};   // middle factor: first chunk of each block
 };
+
+// Compile-time phase shape of an on-the-fly middle factor: the distance form
+// in both precisions; FP32 fixes the shapes of the other workload families,
+// FP64 takes the general one.
+template <class R>
+inline int s_shape(const DevStage<R>& ds) {
+    if (ds.s_dist) return kShapeDistance;
+    return sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0;
+}
 
 }  // namespace midbf_gpu
 

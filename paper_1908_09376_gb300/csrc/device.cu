@@ -361,6 +361,22 @@ void phase_split(const Phase& ph, const Block& bk, int P, int Q, SplitOut& rows,
         }
         return;
     }
+    if (fam == MIDBF_PHASE_DISTANCE) {
+        // |x - xi| in the distance form: coordinates relative to the block's
+        // first column point xi0 (formed in FP64), missing axes zero
+        const double* w0 = &ph.W[(size_t)j0 * d];
+        for (size_t i = 0; i < nr; ++i) {
+            const double* x = &ph.X[(size_t)bk.xidx[i] * d];
+            rows.a[i] = 0.0;
+            for (int k = 0; k < Q; ++k) rows.c[i * Q + k] = k < d ? x[k] - w0[k] : 0.0;
+        }
+        for (size_t j = 0; j < nc; ++j) {
+            const double* w = &ph.W[(size_t)bk.widx[j] * d];
+            cols.a[j] = 0.0;
+            for (int k = 0; k < Q; ++k) cols.c[j * Q + k] = k < d ? w[k] - w0[k] : 0.0;
+        }
+        return;
+    }
     // DOT and FIO families: x.xi = x0.xi + (x - x0).xi0 + (x - x0).(xi - xi0)
     const double* x0 = &ph.X[(size_t)i0 * d];
     const double* w0 = &ph.W[(size_t)j0 * d];
@@ -417,6 +433,7 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
         case MIDBF_PHASE_DOT: P = ph.d; break;
         case MIDBF_PHASE_FIO2D: case MIDBF_PHASE_FIO3D: P = ph.d; Q = ph.d; break;
         case MIDBF_PHASE_FIO2D_JUMP: P = ph.d + 1; Q = ph.d; break;
+        case MIDBF_PHASE_DISTANCE: P = 0; Q = 3; ds.s_dist = true; break;
         default: break;
     }
     if (P > 8 || Q > 3) fail(MIDBF_EINVAL, "on-the-fly middle factor supports at most 8 low-rank terms");

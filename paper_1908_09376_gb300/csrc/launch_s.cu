@@ -25,8 +25,8 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
 }
 
 // FP32: 128-row items for up to 4 RHS per pass, phase shape fixed at compile
-// time for the workload families.  FP64: the general shape (the plain form
-// stores the middle factor by default).
+// time for the workload families.  FP64: the general shape or the distance
+// form (the plain form stores the middle factor by default).
 template <class R, bool CJ, int PQ>
 void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     if constexpr (sizeof(R) == 4) {
@@ -38,23 +38,25 @@ void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, 
             default: launch_s_t<R, 2, 16, CJ, PQ>(ds, src, dst, nrhs, s, persist);
         }
     } else {
+        constexpr int PQ64 = PQ == kShapeDistance ? kShapeDistance : 0;
         switch (nr) {
-            case 1: launch_s_t<R, 2, 1, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            case 2: launch_s_t<R, 2, 2, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            case 4: launch_s_t<R, 2, 4, CJ, 0>(ds, src, dst, nrhs, s, persist); break;
-            default: launch_s_t<R, 2, 8, CJ, 0>(ds, src, dst, nrhs, s, persist);
+            case 1: launch_s_t<R, 2, 1, CJ, PQ64>(ds, src, dst, nrhs, s, persist); break;
+            case 2: launch_s_t<R, 2, 2, CJ, PQ64>(ds, src, dst, nrhs, s, persist); break;
+            case 4: launch_s_t<R, 2, 4, CJ, PQ64>(ds, src, dst, nrhs, s, persist); break;
+            default: launch_s_t<R, 2, 8, CJ, PQ64>(ds, src, dst, nrhs, s, persist);
         }
     }
 }
 
 template <class R, bool CJ>
 void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
-    switch (sizeof(R) == 4 ? phase_shape_code(ds.ss.P, ds.ss.Q) : 0) {
+    switch (s_shape(ds)) {
         case 1: launch_s_pq<R, CJ, 1>(ds, src, dst, nrhs, nr, s, persist); break;
         case 2: launch_s_pq<R, CJ, 2>(ds, src, dst, nrhs, nr, s, persist); break;
         case 3: launch_s_pq<R, CJ, 3>(ds, src, dst, nrhs, nr, s, persist); break;
         case 4: launch_s_pq<R, CJ, 4>(ds, src, dst, nrhs, nr, s, persist); break;
         case 5: launch_s_pq<R, CJ, 5>(ds, src, dst, nrhs, nr, s, persist); break;
+        case kShapeDistance: launch_s_pq<R, CJ, kShapeDistance>(ds, src, dst, nrhs, nr, s, persist); break;
         default: launch_s_pq<R, CJ, 0>(ds, src, dst, nrhs, nr, s, persist);
     }
 }

@@ -38,12 +38,13 @@ void launch_tc_t(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv
 template <bool RF, bool CJ>
 void launch_tc_rc(const DevStage<float>& ds, VecRef<float> dst, int R, const __nv_bfloat16* bimg, int* status,
                   cudaStream_t s) {
-    switch (phase_shape_code(ds.ss.P, ds.ss.Q)) {
+    switch (s_shape(ds)) {
         case 1: launch_tc_t<1, RF, CJ>(ds, dst, R, bimg, status, s); break;
         case 2: launch_tc_t<2, RF, CJ>(ds, dst, R, bimg, status, s); break;
         case 3: launch_tc_t<3, RF, CJ>(ds, dst, R, bimg, status, s); break;
         case 4: launch_tc_t<4, RF, CJ>(ds, dst, R, bimg, status, s); break;
         case 5: launch_tc_t<5, RF, CJ>(ds, dst, R, bimg, status, s); break;
+        case kShapeDistance: launch_tc_t<kShapeDistance, RF, CJ>(ds, dst, R, bimg, status, s); break;
         default: launch_tc_t<0, RF, CJ>(ds, dst, R, bimg, status, s);
     }
 }

@@ -4,7 +4,9 @@
 // with c1 = (2 + sin 2pi x1 sin 2pi x2)/16 and c2 = (2 + cos 2pi x1 cos 2pi x2)/16.
 // FIO3D uses c_k = (2 + sin 2pi x_k cos 2pi x_{k+1})/16 (cyclic); FIO2D_JUMP adds
 // 0.5 |xi| sign(x1 - 0.5) with sign(0) = +1 (one discontinuity, allowed by the
-// piecewise-smooth setting of eq. (1)); DOT is the Fourier phase of Example 2.
+// piecewise-smooth setting of eq. (1)); DOT is the Fourier phase of Example 2;
+// DISTANCE is |x - xi|, the Helmholtz phase h |x - xi| of Example 3 once the
+// points are scaled by h.
 #include "internal.hpp"
 
 namespace midbf {
@@ -18,6 +20,11 @@ double Phase::eval_xy(const double* x, const double* w) const {
             return dot;
         case MIDBF_PHASE_ZERO:
             return 0.0;
+        case MIDBF_PHASE_DISTANCE: {
+            double s = 0.0;
+            for (int k = 0; k < d; ++k) s += (x[k] - w[k]) * (x[k] - w[k]);
+            return std::sqrt(s);
+        }
         case MIDBF_PHASE_SEPARABLE: {
             double a = 0.0, b = 0.0;
             for (int k = 0; k < d; ++k) {
@@ -68,6 +75,7 @@ void phase_check(const Phase& ph) {
         case MIDBF_PHASE_DOT:
         case MIDBF_PHASE_ZERO:
         case MIDBF_PHASE_SEPARABLE:
+        case MIDBF_PHASE_DISTANCE:
             break;
         case MIDBF_PHASE_LOWRANK:
             if (ph.r <= 0 || (int64_t)ph.U.size() != ph.nx * ph.r || (int64_t)ph.V.size() != ph.nw * ph.r)

@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
         const int row = ptid & (kTcM - 1), cq = ptid >> 7;
         const int i = it.y + row;
         const bool rok = i < nrow;
-        float ra = 0.f, ru[Sh::P], rc[Sh::Q > 0 ? Sh::Q : 1];
+        float ra = 0.f, ru[Sh::PA], rc[Sh::QA];
         {
             const int ii = rok ? i : 0;
             ra = rs.a[ro + ii];
@@ -552,8 +552,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
                     if (Sh::Q > 0 && (Sh::fixed || Q > 0)) {
                         float sq = 0.f;
 #pragma unroll
-                        for (int q = 0; q < Sh::Q; ++q)
-                            if (Sh::fixed || q < Q) sq = fmaf(rc[q], cj[1 + P + q], sq);
+                        for (int q = 0; q < Sh::Q; ++q) {
+                            if (!(Sh::fixed || q < Q)) continue;
+                            if constexpr (Sh::dist) {
+                                const float dq = rc[q] - cj[1 + P + q];
+                                sq = fmaf(dq, dq, sq);
+                            } else {
+                                sq = fmaf(rc[q], cj[1 + P + q], sq);
+                            }
+                        }
                         thp += sqrtf(sq);
                     }
                     thp -= rintf(thp);
