@@ -584,6 +584,21 @@ void set_smem_ptr(const void* kernel, size_t bytes) {
     done.insert({kernel, dev});
 }
 
+// Streaming multiprocessors of the current device (cached per device).
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cache[dev] = std::max(1, nsm);
+    return cache[dev];
+}
+
 // Grid of a SIMT launch: one CTA per work item, or (persistent) as many CTAs
 // as are resident on the GPU at once, each looping over the items with the
 // grid size as stride (the kernels' item loops).

@@ -25,13 +25,19 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
 }
 
 // FP32: 128-row items for up to 4 RHS per pass, phase shape fixed at compile
-// time for the workload families.  FP64: the general shape or the distance
-// form (the plain form stores the middle factor by default).
+// time for the workload families; one RHS on a middle factor of few large
+// blocks (fewer 128-row items than two per SM) runs as 64-row items, which
+// doubles the CTAs.  FP64: the general shape or the distance form (the plain
+// form stores the middle factor by default).
 template <class R, bool CJ, int PQ>
 void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     if constexpr (sizeof(R) == 4) {
+        const bool few = (CJ ? ds.n_items_cols4 : ds.n_items_rows4) < 2 * sm_count();
         switch (nr) {
-            case 1: launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
+            case 1:
+                if (few) launch_s_t<R, 2, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist);
+                else launch_s_t<R, 4, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist);
+                break;
             case 2: launch_s_t<R, 4, 2, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
             case 4: launch_s_t<R, 4, 4, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
             case 8: launch_s_t<R, 2, 8, CJ, PQ>(ds, src, dst, nrhs, s, persist); break;
