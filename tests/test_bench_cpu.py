@@ -54,3 +54,25 @@ def test_workload_defaults():
     A.workload = "fio2d_jump"
     w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
     assert (w.N, nrhs, mode, store, tune, graph) == (1024 * 1024, 16, "fp32", "fp32", True, True)
+    A.workload, A.n = "nuft3d", None
+    w, nrhs, mode, *_ = bench.pick_workload(A)
+    assert (w.d, w.nx, w.nw, nrhs, mode, w.x_kind, w.w_kind) == (3, 64 ** 3, 64 ** 3, 1, "fp32", "random", "random")
+    A.workload = "helmholtz"
+    w, nrhs, mode, *_ = bench.pick_workload(A)
+    assert (w.nx, w.nw, nrhs, mode, w.t, w.n0) == (20609, 20353, 1, "fp32", 5.0, 128)
+
+
+def test_sampled_direct_error_rectangular():
+    """|X| != |Omega| (the sphere halves): rows index X, columns index Omega."""
+    bench = _bench()
+    X0, W0 = synth.hemispheres(synth.icosphere(2)[0])
+    ph = mb.Phase.closed_form(synth.PHASE_DISTANCE, 2.0 * X0, 2.0 * W0)
+    oph = OPhase(synth.PHASE_DISTANCE, 2.0 * X0, 2.0 * W0)
+    nx, nw = len(X0), len(W0)
+    assert nx != nw
+    F = synth.complex_gaussian(nw, 2, 0)
+    G = np.stack([direct.direct_sum(oph, F[:, r]) for r in range(2)], 1)
+    H = np.stack([direct.direct_adjoint(oph, G[:, r]) for r in range(2)], 1)
+    ef, ea = bench.sampled_direct_error(ph, F.T, G.T, G.T, H.T, synth.sample_rows(nx, 30, 3),
+                                        synth.sample_rows(nw, 30, 4))
+    assert ef < 1e-13 and ea < 1e-13
