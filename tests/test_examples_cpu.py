@@ -73,3 +73,29 @@ def test_library_recovery_tau_study_of_table3():
             ph = mb.Phase.recover(X, W, rows, cols, r=4, q=2, tau=tau, max_disc=1 << 30, seed=0)
             assert ph.info["disc_rows"] == 0 and ph.info["disc_cols"] == 0, (n, tau)
             assert ph.info["tau"] == tau and ph.info["mismatches"] == 0
+
+
+def test_recovered_phase_pipeline_of_table4():
+    """Example 2 end to end through the library: recover Psi (Algorithm 7),
+    build the MIDBF from it, apply (the oracle applies the exported plan) and
+    compare with the direct sum of the true phase.  Table 4 at n = 16: r = 3
+    fails (eps^b 0.26), r = 4 and 5 reach eps^b 1.1e-6."""
+    n = 16
+    N = n ** 3
+    X = synth.uniform_random_points(N, 3, 0)
+    W = synth.uniform_random_points(N, 3, 1)
+    P = OPhase(synth.PHASE_DOT, X, W)
+    rows = lambda i: np.exp(2j * np.pi * P(i[:, None], np.arange(N)[None, :]))
+    cols = lambda i: np.exp(2j * np.pi * P(np.arange(N)[:, None], i[None, :]))
+    f = synth.complex_gaussian(N, 1, 0)[:, 0]
+    S = synth.sample_rows(N, 200, 3)
+    ref = direct.direct_sum(P, f, rows=S)
+    box = (np.zeros(3), 1.0)
+    for r, bound in ((3, None), (4, 1.1e-5), (5, 1.1e-5)):
+        ph = mb.Phase.recover(X, W, rows, cols, r=r, q=2, tau=0.25, seed=0)
+        plan = mb.Plan.build(ph, tol=1e-6, n0=512, boxX=box, boxW=box)
+        eb = direct.rel_l2(midbf.apply(planio.read(plan.export()), f)[S], ref)
+        if bound is None:
+            assert eb > 0.1, (r, eb)
+        else:
+            assert eb < bound, (r, eb)

@@ -153,3 +153,35 @@ def test_tau_study_of_table3():
     counts = [_oracle_detections(8, t)[0] for t in (1 / 4, 1 / 6, 1 / 8, 1 / 10)]
     assert counts == sorted(counts) and counts[-1] > 0
     assert _oracle_detections(16, 1 / 10)[0] < counts[-1]
+
+
+def _table4():
+    out = {}
+    for line in open(os.path.join(GOLD, "table4_nuft3d.txt")):
+        if line.strip() and not line.startswith("#"):
+            n, r, eb, ek = line.split()
+            out[(int(n), int(r))] = (float(eb), float(ek))
+    return out
+
+
+def test_recovery_rank_of_table4():
+    """Table 4: Algorithm 7 on Example 2 fails at r = 3 (eps^K ~ 0.3) and is
+    exact to rounding at r = 4 and 5 (eps^K ~ 1e-14): x.xi has rank 3 and the
+    unwrap adds integer offsets per recovered vector."""
+    n = 16
+    N = n ** 3
+    X = synth.uniform_random_points(N, 3, 0)
+    W = synth.uniform_random_points(N, 3, 1)
+    P = OPhase(synth.PHASE_DOT, X, W)
+    wr = lambda idx: (lambda p: p - np.rint(p))(P(idx[:, None], np.arange(N)[None, :]))
+    wc = lambda idx: (lambda p: p - np.rint(p))(P(np.arange(N)[:, None], idx[None, :]))
+    S = synth.sample_rows(N, 200, 3)
+    table = _table4()
+    PX, PW = recovery.recovery_path(X), recovery.recovery_path(W)
+    for r in (3, 4, 5):
+        U, V, rec = recovery.low_rank_phase(wr, wc, X, W, r=r, q=2, seed=0, P1=PX, P2=PW)
+        ek = recovery.eps_K(P, U, V, S)
+        if table[(n, r)][1] > 0.1:
+            assert ek > 0.1, (r, ek)
+        else:
+            assert ek < 1e-12 and rec.mismatches == 0, (r, ek)
