@@ -99,3 +99,19 @@ def test_recovered_phase_pipeline_of_table4():
             assert eb > 0.1, (r, eb)
         else:
             assert eb < bound, (r, eb)
+
+
+def test_helmholtz_accuracy_of_table5():
+    """Example 3 with the closed-form phase at the paper's tolerance 1e-9:
+    the MIDBF's eps^b on the level-5 mesh (10,242 nodes) is within 10x of
+    Table 5's 2.79e-8 for n = 10240."""
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden", "table5_helmholtz.txt")
+    eb_paper = {int(l.split()[0]): float(l.split()[1]) for l in open(gold) if l.strip() and not l.startswith("#")}
+    w = synth.Workload("helmholtz_l5_tol9", 3, 5, synth.PHASE_DISTANCE, 1e-9, 64, 1, 0, x_kind="sphere",
+                       w_kind="sphere", t=5.0)
+    plan, P = _library_plan(w, w.t)
+    f = w.rhs(1)[:, 0]
+    S = synth.sample_rows(w.nx, 200, 3)
+    eb = direct.rel_l2(midbf.apply(planio.read(plan.export()), f)[S], direct.direct_sum(P, f, rows=S))
+    assert eb < 10 * eb_paper[10240], eb
