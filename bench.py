@@ -252,10 +252,10 @@ def peaks():
 class OracleSample:
     """The oracle's apply (its sparse factor product, FP64) on a bounded sample
     of the plan: every `sample_every`-th block of every stage, forward and
-    adjoint; times scale to the whole plan by the fraction of factor entries
-    sampled."""
+    adjoint, for `nrhs` right-hand sides at once; times scale to the whole plan
+    by the fraction of factor entries sampled."""
 
-    def __init__(self, plan_bytes, sample_every=32):
+    def __init__(self, plan_bytes, sample_every=32, nrhs=1):
         from oracle import midbf as omidbf
         from oracle import planio
         fac = planio.read(plan_bytes)
@@ -270,15 +270,15 @@ class OracleSample:
             pick = list(range(0, len(st.blocks), sample_every))
             sub = omidbf.Stage(st.kind, st.in_space, st.out_len, st.out_user, [st.blocks[i] for i in pick])
             M = omidbf.stage_matrix(fac, sub, in_len)
-            v = rng.standard_normal(in_len) + 1j * rng.standard_normal(in_len)
-            w = rng.standard_normal(st.out_len) + 1j * rng.standard_normal(st.out_len)
+            v = rng.standard_normal((in_len, nrhs)) + 1j * rng.standard_normal((in_len, nrhs))
+            w = rng.standard_normal((st.out_len, nrhs)) + 1j * rng.standard_normal((st.out_len, nrhs))
             self.parts.append((M, M.conj().T.tocsr(), v, w))
             total += sum(ent)
             sampled += sum(ent[i] for i in pick)
             in_len = st.out_len
         self.scale = total / max(1, sampled)
         self.desc = (f"every {sample_every}th block of each stage ({sampled} of {total} factor entries); "
-                     f"forward+adjoint sparse FP64 apply; time scaled by the entry ratio")
+                     f"forward+adjoint sparse FP64 apply of {nrhs} RHS; time scaled by the entry ratio")
 
     def step_seconds(self):
         t0 = time.perf_counter()
@@ -288,40 +288,48 @@ class OracleSample:
         return (time.perf_counter() - t0) * self.scale
 
 
-def cpu_baseline(plan_bytes, n_points, seconds_budget=15.0):
-    smp = OracleSample(plan_bytes)
+def cpu_baseline(plan_bytes, n_points, seconds_budget=15.0, nrhs=1):
+    """n_points: outputs of one forward + adjoint step per RHS (|X| + |Omega|)."""
+    smp = OracleSample(plan_bytes, nrhs=nrhs)
     times = []
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds_budget or len(times) < 3:
         times.append(smp.step_seconds())
     step_s = statistics.median(times)
-    return {"value": 2 * n_points / step_s, "unit": "points*RHS/s", "cores": smp.cores, "kind": "oracle",
+    return {"value": n_points * nrhs / step_s, "unit": "points*RHS/s", "cores": smp.cores, "kind": "oracle",
             "sample": smp.desc + f"; median of {len(times)} repetitions"}
 
 
 def run_reference(args, ws, rank):
-    """Reference arm: the CPU oracle's apply as it stands, on the host cores."""
+    """Reference arm: the CPU oracle's apply as it stands, on the host cores,
+    on this arm's workload (its plan built by the library on the host)."""
     if rank != 0:
         return
+    if args.workload in ("batched", "fio2d_jump"):
+        why = ("32 plans built on the GPU" if args.workload == "batched" else
+               "the n = 1024 plan (1.6e10 T entries) is built on the GPU and does not fit the host twice")
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle arm not run for {args.workload}: {why}"}),
+              flush=True)
+        return
     import paper_1908_09376_gb300 as mb
-    n = args.n or 256
-    X, W, bx, bw = workload(n)
-    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=64, boxX=bx, boxW=bw,
-                         nthreads=args.threads)
-    smp = OracleSample(plan.export())
+    wl, R1, *_ = pick_workload(args)
+    X, W, bx, bw = wl.points()
+    plan = mb.Plan.build(mb.Phase.closed_form(wl.phase, X, W), tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw,
+                         nthreads=args.threads, t=wl.t)
+    smp = OracleSample(plan.export(), nrhs=R1)
     del plan
-    N = n ** 2
+    units = (wl.nx + wl.nw) * R1
     for _ in range(args.warmup):
         smp.step_seconds()
     times = [smp.step_seconds() for _ in range(args.steps)]
     step_s = sum(times) / len(times)
-    v = 2 * N / step_s
+    v = units / step_s
     cpu = {"value": v, "unit": "points*RHS/s", "cores": smp.cores, "kind": "oracle", "sample": smp.desc}
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "points*RHS/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": f"fio2d_n{n}", "N": N, "nrhs": 1, "tol": 1e-6, "n0": 64,
-                      "step": "forward + adjoint apply"},
+           "config": {"workload": wl.name, "N": wl.N, "nx": wl.nx, "nw": wl.nw, "nrhs": R1, "tol": wl.tol,
+                      "n0": wl.n0, "step": "forward + adjoint apply"},
            "cpu_baseline": cpu, "e2e": {"value": v, "unit": "points*RHS/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -510,6 +518,10 @@ def main():
     t0 = time.perf_counter()
     mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[mode_name]
     keep_plan = args.workload == "fio2d" and not args.skip_extras and R1 == 1
+    # the oracle's baseline needs the plan file; the small workloads export it before the upload
+    # consumes the host copy (the n = 1024 plan is too large to hold twice)
+    want_cpu = rank == 0 and ws == 1 and not args.skip_extras and args.workload not in ("fio2d_jump",)
+    plan_bytes = plan.export() if want_cpu and not keep_plan else None
     # large plans: hand the coefficients to the device as they are uploaded
     dp32 = mb.DevicePlan(plan, mode, mb.S_ONTHEFLY, consume=not keep_plan)
     t_up = time.perf_counter() - t0
@@ -778,9 +790,9 @@ def main():
            "d2h_bytes_per_step": (nx + nw) * R1 * 8, "ms_per_step": round(e2e_s * 1e3, 4)}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.skip_extras and R1 == 1 and args.workload == "fio2d":
+    if want_cpu:
         try:
-            cpu = cpu_baseline(plan.export(), N)
+            cpu = cpu_baseline(plan_bytes if plan_bytes is not None else plan.export(), nx + nw, nrhs=R1)
         except Exception as e:  # the GPU numbers stand without it
             cpu = {"error": f"{type(e).__name__}: {e}"}
 

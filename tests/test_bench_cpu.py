@@ -76,3 +76,24 @@ def test_sampled_direct_error_rectangular():
     ef, ea = bench.sampled_direct_error(ph, F.T, G.T, G.T, H.T, synth.sample_rows(nx, 30, 3),
                                         synth.sample_rows(nw, 30, 4))
     assert ef < 1e-13 and ea < 1e-13
+
+
+def test_reference_arm_json_line():
+    """--impl reference times the oracle on the selected workload (host only)
+    and prints the contract's JSON line; the GPU-built workloads say why not."""
+    import json
+    import os
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "helmholtz", "--n", "3", "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, env=env, timeout=300, check=True).stdout
+    d = json.loads(out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["config"]["workload"] == "helmholtz_l3" and (d["config"]["nx"], d["config"]["nw"]) == (337, 305)
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                          "batched"], capture_output=True, text=True, env=env, timeout=300, check=True).stdout
+    d = json.loads(out.strip().splitlines()[-1])
+    assert d["impl"] == "reference" and "unavailable" in d
