@@ -101,14 +101,6 @@ def aggregate(total_ms_local, units_per_step_per_rank, steps, pg=None, device=No
     return ms_per_step, world * units_per_step_per_rank / (ms_per_step * 1e-3)
 
 
-def workload(n):
-    X = synth.uniform_grid(n, 2)
-    W = synth.frequency_grid(n, 2)
-    boxX = (np.zeros(2), 1.0)
-    boxW = (np.full(2, -n / 2), float(n))
-    return X, W, boxX, boxW
-
-
 def pick_workload(args):
     """The synthetic workload, its RHS count, arithmetic and build site."""
     if args.workload == "fio2d":
