@@ -219,6 +219,15 @@ void midbf_dplan_destroy(midbf_dplan* dp);
  * invalid).  Reading synchronizes the device; reset = 1 clears the word. */
 int midbf_dplan_status(const midbf_dplan* dp, int reset, int* status);
 
+/* Failure-detection self-test of the bounded waits (no GPU fault involved):
+ * launches ctas (1..1024) one-thread CTAs on stream (a cudaStream_t) that
+ * each wait, with the tensor-core kernels' bounded wait (2 s limit), on an
+ * mbarrier nothing arrives on.  Each gives up, sets the plan's status word to
+ * MIDBF_ETIMEOUT and exits; midbf_dplan_status then reads MIDBF_ETIMEOUT and
+ * the context stays usable.  Asynchronous.  Errors: MIDBF_EINVAL (bad
+ * arguments, or the stream is being recorded into a graph). */
+int midbf_wait_selftest(midbf_dplan* dp, int ctas, void* stream);
+
 /* Bytes of device workspace midbf_apply needs for nrhs right-hand sides. */
 int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes);
 

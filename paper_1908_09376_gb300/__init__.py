@@ -101,6 +101,7 @@ midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
                          [_vp, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_int), _dblp, C.POINTER(C.c_int)])
 midbf_autotune = _sig("midbf_autotune", C.c_int, [_vp, C.c_int, _vp])
+midbf_wait_selftest = _sig("midbf_wait_selftest", C.c_int, [_vp, C.c_int, _vp])
 midbf_set_choice = _sig("midbf_set_choice", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int])
 midbf_get_choice = _sig("midbf_get_choice", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)])
 midbf_capture_begin = _sig("midbf_capture_begin", C.c_int, [_vp])
@@ -300,6 +301,13 @@ class DevicePlan:
         if getattr(self, "h", None):
             midbf_dplan_destroy(self.h)
             self.h = None
+
+    def wait_selftest(self, ctas=4, stream=None):
+        """Failure-detection self-test: bounded waits that run out set MIDBF_ETIMEOUT
+        in this plan's status word (read it with status())."""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        check(midbf_wait_selftest(self.h, ctas, s.cuda_stream), "midbf_wait_selftest")
 
     def status(self, reset=True):
         v = C.c_int()

@@ -158,6 +158,7 @@ int forced_or_pick(int force, int nrhs, const std::function<size_t(int)>& smem) 
 // Grid of a persistent SIMT launch (device.cu).
 int grid_for(const void* kernel, size_t smem, int nitems, bool persist);
 int sm_count();
+void launch_wait_selftest(int* status, int ctas, cudaStream_t s);
 
 constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
 constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages

@@ -951,6 +951,19 @@ int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags
 
 void midbf_dplan_destroy(midbf_dplan* dp) { delete dp; }
 
+int midbf_wait_selftest(midbf_dplan* dp, int ctas, void* stream) {
+    try {
+        if (!dp || ctas <= 0 || ctas > 1024) fail(MIDBF_EINVAL, "bad argument");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        if (capturing(s)) fail(MIDBF_EINVAL, "the self-test cannot be recorded into a graph");
+        midbf_gpu::launch_wait_selftest(dp->d_status, ctas, s);
+        return MIDBF_OK;
+    } catch (const Error& e) {
+        set_last_error(e.what());
+        return e.code;
+    }
+}
+
 int midbf_dplan_status(const midbf_dplan* dp, int reset, int* status) {
     try {
         if (!dp || !status) fail(MIDBF_EINVAL, "null argument");

@@ -94,4 +94,21 @@ void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<f
 
 // Bytes of the B-image area of the workspace for nrhs RHS (0 outside the
 // tensor-core modes): the largest stage's chunks at one group of <= kTcR RHS.
+
+// Self-test of the failure detection: one thread per CTA waits, with the
+// bounded wait of the tensor-core pipelines, on an mbarrier that nothing
+// arrives on.  The wait gives up after its time limit (or at once when
+// another CTA has already set the status word), the thread sets
+// MIDBF_ETIMEOUT and the CTA exits; no TMEM, no bulk copy is involved.
+__global__ void k_wait_selftest(int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    if (!mbar_wait(&bar, 0, status)) atomicExch(status, MIDBF_ETIMEOUT);
+}
+
+void launch_wait_selftest(int* status, int ctas, cudaStream_t s) {
+    k_wait_selftest<<<ctas, 1, 0, s>>>(status);
+    CK(cudaGetLastError());
+}
 }  // namespace midbf_gpu
