@@ -338,10 +338,31 @@ struct IdOut {
 
 }  // namespace
 
-// Construction timings on stderr when the environment sets MIDBF_BUILD_LOG.
+// Construction timings on stderr when the environment sets MIDBF_BUILD_LOG:
+// wall time per phase, and the thread-seconds spent filling kernel samples
+// and in the pivoted QRs of the host IDs.
 struct BuildLog {
     bool on = std::getenv("MIDBF_BUILD_LOG") != nullptr;
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now(), t = t0;
+    std::atomic<int64_t> ns_fill{0}, ns_qr{0}, entries{0};
+    template <class F>
+    auto timed(std::atomic<int64_t>& acc, F&& f) {
+        if (!on) return f();
+        const auto a = std::chrono::steady_clock::now();
+        struct Add {
+            std::atomic<int64_t>& acc;
+            std::chrono::steady_clock::time_point a;
+            ~Add() {
+                acc += std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now() - a).count();
+            }
+        } add{acc, a};
+        return f();
+    }
+    void totals() {
+        if (!on) return;
+        std::fprintf(stderr, "[midbf build] host IDs: %.2f thread-s filling %.3g kernel samples, %.2f thread-s in QRs\n",
+                     ns_fill.load() * 1e-9, (double)entries.load(), ns_qr.load() * 1e-9);
+    }
     void mark(const std::string& what) {
         if (!on) return;
         const auto now = std::chrono::steady_clock::now();
@@ -416,8 +437,11 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
             std::vector<int64_t> pos = mock_chebyshev(cand.xy, cand.nn, d, ns, seed);
             std::vector<int64_t> srows(pos.size());
             for (size_t i = 0; i < pos.size(); ++i) srows[i] = cand.pts[pos[i]];
-            kernel_fill(M, srows, !cols_x, cols);
-            IdResult r = column_id(M, (int)srows.size(), (int)cols.size(), prm.tol, prm.kmax);
+            blog.timed(blog.ns_fill, [&] { kernel_fill(M, srows, !cols_x, cols); });
+            blog.entries += (int64_t)(srows.size() * cols.size());
+            IdResult r = blog.timed(blog.ns_qr, [&] {
+                return column_id(M, (int)srows.size(), (int)cols.size(), prm.tol, prm.kmax);
+            });
             const int64_t k = (int64_t)r.skel.size();
             const int64_t need = (int64_t)std::ceil(prm.t * (double)k);
             if ((int64_t)pos.size() >= ncand || (int64_t)pos.size() >= need) {
@@ -604,6 +628,7 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
     }
 
     blog.mark("IDs done");
+    blog.totals();
     // ---- assemble the stages in forward order ----
     // ypos[(ib, ip)] = (offset, k) of y(beta, P_k) in the previous V stage output
     std::vector<std::pair<int64_t, int>> ypos, zpos;
