@@ -421,9 +421,8 @@ std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm) {
         // sample on the opposite side of the decomposed index set.
         const size_t ms = srows.size();
         M.resize(ms * cols.size());
-        for (size_t c = 0; c < cols.size(); ++c)
-            for (size_t s = 0; s < ms; ++s)
-                M[c * ms + s] = srows_are_x ? ph.kernel(srows[s], cols[c]) : ph.kernel(cols[c], srows[s]);
+        if (srows_are_x) ph.kernel_block(srows.data(), ms, cols.data(), cols.size(), M.data(), 1, ms);
+        else ph.kernel_block(cols.data(), cols.size(), srows.data(), ms, M.data(), ms, 1);
     };
 
     // Column ID of the index set `cols` (points on side `cols_x`) from a sample

@@ -93,6 +93,11 @@ struct Phase {
         }
         return eval_xy(&X[(size_t)i * d], &W[(size_t)j * d]);
     }
+    // K(xi[a], wj[b]) into out[a * sx + b * sw] for a < na, b < nb: the same
+    // formulas as kernel(), with the parts that depend on one point only
+    // (the FIO coefficients c_k(x), |xi|, ...) evaluated once per point.
+    void kernel_block(const int64_t* xi, size_t na, const int64_t* wj, size_t nb, cplx* out, size_t sx,
+                      size_t sw) const;
     // exp(2 pi i Phi), Phi reduced modulo one first.
     cplx kernel(int64_t i, int64_t j) const {
         double p = (*this)(i, j);

@@ -59,6 +59,96 @@ double Phase::eval_xy(const double* x, const double* w) const {
     }
 }
 
+namespace {
+
+inline cplx unit(double p) {
+    p -= std::nearbyint(p);
+    double s, c;
+    sincos(2.0 * M_PI * p, &s, &c);
+    return cplx(c, s);
+}
+
+}  // namespace
+
+void Phase::kernel_block(const int64_t* xi, size_t na, const int64_t* wj, size_t nb, cplx* out, size_t sx,
+                         size_t sw) const {
+    const double twopi = 2.0 * M_PI;
+    auto xp = [&](size_t a) { return &X[(size_t)xi[a] * d]; };
+    auto wp = [&](size_t b) { return &W[(size_t)wj[b] * d]; };
+    auto dot = [&](const double* x, const double* w) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += x[k] * w[k];
+        return s;
+    };
+    switch (family) {
+        case MIDBF_PHASE_FIO2D:
+        case MIDBF_PHASE_FIO2D_JUMP: {
+            // per row: c1^2, c2^2 (and the sign of x1 - 1/2); per column: |xi| / 2
+            const bool jump = family == MIDBF_PHASE_FIO2D_JUMP;
+            std::vector<double> c1s(na), c2s(na), sg(na), hn(jump ? nb : 0);
+            for (size_t a = 0; a < na; ++a) {
+                const double* x = xp(a);
+                const double c1 = (2.0 + std::sin(twopi * x[0]) * std::sin(twopi * x[1])) / 16.0;
+                const double c2 = (2.0 + std::cos(twopi * x[0]) * std::cos(twopi * x[1])) / 16.0;
+                c1s[a] = c1 * c1;
+                c2s[a] = c2 * c2;
+                sg[a] = (x[0] - 0.5 >= 0.0) ? 1.0 : -1.0;
+            }
+            for (size_t b = 0; b < (jump ? nb : 0); ++b) {
+                const double* w = wp(b);
+                hn[b] = 0.5 * std::sqrt(w[0] * w[0] + w[1] * w[1]);
+            }
+            for (size_t b = 0; b < nb; ++b) {
+                const double* w = wp(b);
+                for (size_t a = 0; a < na; ++a) {
+                    double v = dot(xp(a), w) + std::sqrt(c1s[a] * w[0] * w[0] + c2s[a] * w[1] * w[1]);
+                    if (jump) v += hn[b] * sg[a];
+                    out[a * sx + b * sw] = unit(v);
+                }
+            }
+            return;
+        }
+        case MIDBF_PHASE_FIO3D: {
+            std::vector<double> cs(na * 3);
+            for (size_t a = 0; a < na; ++a) {
+                const double* x = xp(a);
+                for (int k = 0; k < 3; ++k) {
+                    const double ck = (2.0 + std::sin(twopi * x[k]) * std::cos(twopi * x[(k + 1) % 3])) / 16.0;
+                    cs[a * 3 + k] = ck * ck;
+                }
+            }
+            for (size_t b = 0; b < nb; ++b) {
+                const double* w = wp(b);
+                for (size_t a = 0; a < na; ++a) {
+                    double acc = 0.0;
+                    for (int k = 0; k < 3; ++k) acc += cs[a * 3 + k] * w[k] * w[k];
+                    out[a * sx + b * sw] = unit(dot(xp(a), w) + std::sqrt(acc));
+                }
+            }
+            return;
+        }
+        case MIDBF_PHASE_SEPARABLE: {
+            std::vector<double> ra(na), cb(nb);
+            for (size_t a = 0; a < na; ++a) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) s += std::sin(twopi * xp(a)[k]);
+                ra[a] = s;
+            }
+            for (size_t b = 0; b < nb; ++b) {
+                double s = 0.0;
+                for (int k = 0; k < d; ++k) s += wp(b)[k] * wp(b)[k];
+                cb[b] = s;
+            }
+            for (size_t b = 0; b < nb; ++b)
+                for (size_t a = 0; a < na; ++a) out[a * sx + b * sw] = unit(ra[a] + 0.05 * cb[b]);
+            return;
+        }
+        default:
+            for (size_t b = 0; b < nb; ++b)
+                for (size_t a = 0; a < na; ++a) out[a * sx + b * sw] = kernel(xi[a], wj[b]);
+    }
+}
+
 void phase_check(const Phase& ph) {
     if (ph.d != 2 && ph.d != 3) fail(MIDBF_EINVAL, "d must be 2 or 3");
     if (ph.nx <= 0 || ph.nw <= 0) fail(MIDBF_EINVAL, "empty point set");
