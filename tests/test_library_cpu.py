@@ -241,3 +241,22 @@ def test_recovery_callback_failure():
     with pytest.raises(mb.MidbfError) as e:
         mb.Phase.recover(X, W, bad, bad, r=2, q=2)
     assert e.value.code == mb.ECALLBACK
+
+
+def test_recovery_partitions_at_a_jump():
+    """Algorithm 6 through the C ABI on a rank-3 phase with a jump of |xi|
+    across x1 = 0: discontinuities are flagged along X, tau stays 1/4, rows
+    and columns agree, and exp(2 pi i Psi) reproduces K to rounding."""
+    from oracle import recovery
+    n = 24
+    X = synth.uniform_grid(n, 2) * 0.3 - 0.15
+    W = synth.frequency_grid(n, 2) * 0.2
+    sg = np.where(X[:, 0] >= 0, 1.0, -1.0)
+    P = OPhase(synth.PHASE_LOWRANK, X, W, np.stack([X[:, 0], X[:, 1], 0.5 * sg], 1),
+               np.stack([W[:, 0], W[:, 1], np.linalg.norm(W, axis=1)], 1))
+    rows, cols = _access(P, n * n)
+    ph = mb.Phase.recover(X, W, rows, cols, r=4, q=2, seed=0)
+    info = ph.info
+    assert info["disc_rows"] > 0 and info["tau"] == 0.25 and info["mismatches"] == 0
+    U, V = ph.factors()
+    assert recovery.eps_K(P, U, V, synth.sample_rows(n * n, 200, 3)) < 1e-12

@@ -269,3 +269,33 @@ def test_low_rank_phase_recovers_smooth_phase():
     assert np.abs(diff - diff[:, :1]).max() < 1e-9 and np.abs(diff - np.rint(diff)).max() < 1e-9
     S = synth.sample_rows(n * n, 200, 3)
     assert recovery.eps_K(ph, U, V, S) < 1e-9
+
+
+def _jump_phase(n=24):
+    """Phi = x.xi + (1/2) sign(x1) |xi| on a small grid: rank 3, with a jump of
+    |xi| across x1 = 0 that is not an integer (a discontinuity for Algorithm 4),
+    and path increments below 1/4 elsewhere."""
+    X = synth.uniform_grid(n, 2) * 0.3 - 0.15
+    W = synth.frequency_grid(n, 2) * 0.2
+    sg = np.where(X[:, 0] >= 0, 1.0, -1.0)
+    U = np.stack([X[:, 0], X[:, 1], 0.5 * sg], 1)
+    V = np.stack([W[:, 0], W[:, 1], np.linalg.norm(W, axis=1)], 1)
+    return X, W, Phase(synth.PHASE_LOWRANK, X, W, U, V)
+
+
+def test_recovery_partitions_at_a_jump():
+    """Algorithm 6: the jump is detected along the X path, Partition2 splits
+    the tree there, and each piece is recovered from its own root, so rows and
+    columns still agree (Lemma 3.2: zero mismatches at tau = 1/4) and
+    exp(2 pi i Psi) reproduces K to rounding for r >= 4 (rank 3 plus the
+    integer offsets); r = 3 cannot hold the offsets."""
+    X, W, ph = _jump_phase()
+    N = X.shape[0]
+    wr = lambda idx: (lambda p: p - np.rint(p))(ph(idx[:, None], np.arange(N)[None, :]))
+    wc = lambda idx: (lambda p: p - np.rint(p))(ph(np.arange(N)[:, None], idx[None, :]))
+    S = synth.sample_rows(N, 200, 3)
+    for r, exact in ((3, False), (4, True), (5, True)):
+        U, V, rec = recovery.low_rank_phase(wr, wc, X, W, r=r, q=2, seed=0, max_disc=64)
+        assert len(rec.Dr) > 1 and rec.tau == 0.25 and rec.mismatches == 0
+        ek = recovery.eps_K(ph, U, V, S)
+        assert (ek < 1e-12) if exact else (ek > 0.1), (r, ek)
