@@ -224,7 +224,9 @@ int midbf_dplan_status(const midbf_dplan* dp, int reset, int* status);
  * each wait, with the tensor-core kernels' bounded wait (2 s limit), on an
  * mbarrier nothing arrives on.  Each gives up, sets the plan's status word to
  * MIDBF_ETIMEOUT and exits; midbf_dplan_status then reads MIDBF_ETIMEOUT and
- * the context stays usable.  Asynchronous.  Errors: MIDBF_EINVAL (bad
+ * the context stays usable.  Asynchronous.  The status word is the plan's:
+ * tensor-core applies of the same plan in flight meanwhile would see it set
+ * and give up, so run the self-test alone.  Errors: MIDBF_EINVAL (bad
  * arguments, or the stream is being recorded into a graph). */
 int midbf_wait_selftest(midbf_dplan* dp, int ctas, void* stream);
 
