@@ -506,6 +506,8 @@ def main():
                          device_ids=1 if build_site == "device" else 0, store_fp32=1 if store == "fp32" else 0)
     t_build = time.perf_counter() - t0
     st = plan.stats()
+    rk = plan.ranks()
+    rank_pcts = {p: int(np.percentile(rk, p)) for p in (10, 50, 90)} if rk.size else None
     log(f"built {wl.name}: {st['t_entries']} T entries, {st['s_entries']} S entries")
     t0 = time.perf_counter()
     mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[mode_name]
@@ -799,7 +801,8 @@ def main():
                       "choices": ([[dp32.choice(R1, q, 0), dp32.choice(R1, q, 1)] for q in range(len(sinfo))]
                                   if tune else None),
                       "t_entries": st["t_entries"], "s_entries": st["s_entries"], "max_rank": st["max_rank"],
-                      "mean_rank": round(st["mean_rank"], 1), "factor_bytes": fbytes, "index_bytes": ibytes,
+                      "mean_rank": round(st["mean_rank"], 1), "rank_percentiles": rank_pcts,
+                      "factor_bytes": fbytes, "index_bytes": ibytes,
                       "l2": "flushed (512 MB write) between timed steps",
                       "parallelism": f"replicas x{ws}", "build_s": round(t_build, 1),
                       "upload_s": round(t_up, 1)},

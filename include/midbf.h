@@ -192,6 +192,13 @@ typedef struct {
 } midbf_stats;
 
 int midbf_plan_stats(const midbf_plan* plan, midbf_stats* st);
+
+/* Ranks k of the interpolative decompositions of one stage (stage index in
+ * [0, nstages)), or of every V/U stage with stage = -1, in plan order:
+ * writes min(count, cap) ranks to ranks (may be NULL with cap = 0) and the
+ * total number of decompositions to *count.  The middle factor holds none.
+ * Errors: MIDBF_EINVAL. */
+int midbf_plan_ranks(const midbf_plan* plan, int stage, int32_t* ranks, int64_t cap, int64_t* count);
 void midbf_plan_destroy(midbf_plan* plan);
 void midbf_free(void* p);
 

@@ -84,6 +84,8 @@ midbf_build = _sig("midbf_build", C.c_int, [_vp, C.POINTER(midbf_params), C.POIN
 midbf_plan_export = _sig("midbf_plan_export", C.c_int, [_vp, C.POINTER(_vp), C.POINTER(C.c_size_t)])
 midbf_plan_import = _sig("midbf_plan_import", C.c_int, [_vp, C.c_size_t, C.POINTER(_vp)])
 midbf_plan_stats = _sig("midbf_plan_stats", C.c_int, [_vp, C.POINTER(midbf_stats)])
+midbf_plan_ranks = _sig("midbf_plan_ranks", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int32), C.c_int64,
+                                                      C.POINTER(C.c_int64)])
 midbf_plan_destroy = _sig("midbf_plan_destroy", None, [_vp])
 midbf_free = _sig("midbf_free", None, [_vp])
 midbf_dplan_create = _sig("midbf_dplan_create", C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp)])
@@ -280,6 +282,15 @@ class Plan:
         st = midbf_stats()
         check(midbf_plan_stats(self.h, C.byref(st)), "midbf_plan_stats")
         return {f: getattr(st, f) for f, _ in midbf_stats._fields_}
+
+    def ranks(self, stage: int = -1) -> np.ndarray:
+        """Ranks k of the interpolative decompositions of one stage (-1: all)."""
+        cnt = C.c_int64()
+        check(midbf_plan_ranks(self.h, stage, None, 0, C.byref(cnt)), "midbf_plan_ranks")
+        out = np.empty(cnt.value, dtype=np.int32)
+        check(midbf_plan_ranks(self.h, stage, out.ctypes.data_as(C.POINTER(C.c_int32)), out.size, C.byref(cnt)),
+              "midbf_plan_ranks")
+        return out
 
 
 class DevicePlan:

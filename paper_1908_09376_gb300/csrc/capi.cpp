@@ -180,6 +180,26 @@ int midbf_plan_stats(const midbf_plan* plan, midbf_stats* st) {
     });
 }
 
+int midbf_plan_ranks(const midbf_plan* plan, int stage, int32_t* ranks, int64_t cap, int64_t* count) {
+    return guarded([&] {
+        if (!plan || !count || cap < 0 || (cap > 0 && !ranks)) fail(MIDBF_EINVAL, "null argument");
+        const Plan& pl = *as_plan(plan);
+        if (stage < -1 || stage >= (int)pl.stages.size()) fail(MIDBF_EINVAL, "stage index out of range");
+        int64_t n = 0;
+        for (size_t q = 0; q < pl.stages.size(); ++q) {
+            if (stage >= 0 && (int)q != stage) continue;
+            const Stage& st = pl.stages[q];
+            if (st.kind == KIND_S) continue;
+            for (const Block& b : st.blocks)
+                for (const Sub& sb : b.subs) {
+                    if (n < cap) ranks[n] = sb.k;
+                    ++n;
+                }
+        }
+        *count = n;
+    });
+}
+
 void midbf_plan_destroy(midbf_plan* plan) { delete reinterpret_cast<Plan*>(plan); }
 
 }  // extern "C"

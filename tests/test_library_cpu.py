@@ -260,3 +260,23 @@ def test_recovery_partitions_at_a_jump():
     assert info["disc_rows"] > 0 and info["tau"] == 0.25 and info["mismatches"] == 0
     U, V = ph.factors()
     assert recovery.eps_K(P, U, V, synth.sample_rows(n * n, 200, 3)) < 1e-12
+
+
+def test_plan_ranks_agree_with_stats_and_the_oracle_reader():
+    """midbf_plan_ranks lists every ID's rank: their count, mean and maximum
+    match midbf_plan_stats, and per stage they equal the ranks the oracle's
+    independent reader finds in the exported file."""
+    n = 32
+    X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16,
+                         boxX=(np.zeros(2), 1.0), boxW=(np.full(2, -n / 2), float(n)))
+    st = plan.stats()
+    allr = plan.ranks()
+    assert allr.size == st["nsubs"] and allr.max() == st["max_rank"]
+    assert abs(allr.mean() - st["mean_rank"]) < 1e-12
+    fac = planio.read(plan.export())
+    for q, stage in enumerate(fac.stages):
+        ref = [s.skel.size for b in stage.blocks for s in b.subs] if stage.kind != midbf.KIND_S else []
+        assert plan.ranks(q).tolist() == ref, q
+    with pytest.raises(mb.MidbfError):
+        plan.ranks(len(fac.stages))
