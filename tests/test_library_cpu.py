@@ -280,3 +280,55 @@ def test_plan_ranks_agree_with_stats_and_the_oracle_reader():
         assert plan.ranks(q).tolist() == ref, q
     with pytest.raises(mb.MidbfError):
         plan.ranks(len(fac.stages))
+
+
+_FUZZ = r"""
+import sys
+import numpy as np
+import synth
+import paper_1908_09376_gb300 as mb
+n = 16
+X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16,
+                     boxX=(np.zeros(2), 1.0), boxW=(np.full(2, -8.0), 16.0))
+data = plan.export()
+rng = np.random.default_rng(int(sys.argv[1]))
+loaded = rejected = 0
+for it in range(300):
+    b = bytearray(data)
+    kind = int(rng.integers(0, 4))
+    if kind == 0:
+        for _ in range(int(rng.integers(1, 4))):
+            b[int(rng.integers(0, len(b)))] ^= int(rng.integers(1, 256))
+    elif kind == 1:
+        pos = int(rng.integers(0, len(b) - 8)) & ~3
+        b[pos:pos + 8] = int(rng.choice([-1, 2**31 - 1, 2**40, -2**33, 0])).to_bytes(8, "little", signed=True)
+    elif kind == 2:
+        b = b[:int(rng.integers(0, len(b)))]
+    else:
+        pos = int(rng.integers(0, len(b) - 4)) & ~3
+        b[pos:pos + 4] = int(rng.choice([-1, 2**31 - 1, 1 << 20, 0, 3])).to_bytes(4, "little", signed=True)
+    try:
+        mb.Plan.load(bytes(b)).stats()
+        loaded += 1
+    except mb.MidbfError as e:
+        assert e.code in (mb.EFORMAT, mb.EINVAL, mb.ENOMEM), e.code
+        rejected += 1
+print(loaded, rejected)
+"""
+
+
+def test_corrupted_plan_files_are_rejected_not_crashed():
+    """300 random corruptions of a plan file (byte flips, huge or negative
+    sizes, truncation): each one loads as a plan that passes validation or is
+    rejected with a status code; the process never crashes (run in a child)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", _FUZZ, "7"], capture_output=True, text=True, env=env,
+                         timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    loaded, rejected = (int(v) for v in out.stdout.split())
+    assert loaded + rejected == 300 and rejected > 200
