@@ -124,7 +124,8 @@ typedef struct {
  * with the restricted randomized SVD into a rank-r phase.  tau: initial
  * discontinuity threshold (paper: 1/4), raised by 1/40 while more than
  * max_disc discontinuities are found, at most to 1/2.  info may be NULL.
- * Errors: MIDBF_EINVAL, MIDBF_ECALLBACK, MIDBF_ERECOVERY. */
+ * Errors: MIDBF_EINVAL, MIDBF_ECALLBACK (a callback failed, or returned a
+ * non-finite or zero value, which has no phase), MIDBF_ERECOVERY. */
 int midbf_phase_recover(int d, int64_t nx, const double* X, int64_t nw, const double* W,
                         const midbf_access* acc, int r, int q, double tau, int max_disc,
                         uint64_t seed, midbf_phase** out, midbf_recover_info* info);

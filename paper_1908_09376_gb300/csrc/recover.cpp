@@ -430,6 +430,14 @@ std::vector<double> pinv(const std::vector<double>& A, int m, int n) {
 
 double wrapped(const cplx& z) { return std::atan2(z.imag(), z.real()) / (2.0 * M_PI); }
 
+// A kernel value e^{2 pi i Phi} has modulus one; a non-finite or zero value
+// from a callback has no phase to recover.
+void check_values(const std::vector<cplx>& buf, const char* what) {
+    for (const cplx& z : buf)
+        if (!std::isfinite(z.real()) || !std::isfinite(z.imag()) || (z.real() == 0.0 && z.imag() == 0.0))
+            fail(MIDBF_ECALLBACK, std::string(what) + " callback returned a non-finite or zero value");
+}
+
 }  // namespace
 
 std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t nw, const double* W,
@@ -440,6 +448,7 @@ std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t
         std::vector<cplx> buf(idx.size() * (size_t)nw);
         if (!idx.empty() && acc.rows_fn(acc.user, idx.data(), (int64_t)idx.size(), reinterpret_cast<double*>(buf.data())))
             fail(MIDBF_ECALLBACK, "rows callback failed");
+        check_values(buf, "rows");
         inf.rows_requested += (int64_t)idx.size();
         std::vector<double> u(buf.size());
         for (size_t i = 0; i < buf.size(); ++i) u[i] = wrapped(buf[i]);
@@ -449,6 +458,7 @@ std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t
         std::vector<cplx> buf(idx.size() * (size_t)nx);
         if (!idx.empty() && acc.cols_fn(acc.user, idx.data(), (int64_t)idx.size(), reinterpret_cast<double*>(buf.data())))
             fail(MIDBF_ECALLBACK, "columns callback failed");
+        check_values(buf, "columns");
         inf.cols_requested += (int64_t)idx.size();
         std::vector<double> u(buf.size());
         for (size_t i = 0; i < buf.size(); ++i) u[i] = wrapped(buf[i]);

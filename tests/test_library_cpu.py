@@ -241,6 +241,13 @@ def test_recovery_callback_failure():
     with pytest.raises(mb.MidbfError) as e:
         mb.Phase.recover(X, W, bad, bad, r=2, q=2)
     assert e.value.code == mb.ECALLBACK
+    # values without a phase: NaN, or zero modulus
+    for v in (np.nan + 0j, 0j):
+        rows = lambda idx: np.full((len(idx), 64), v)
+        cols = lambda idx: np.full((64, len(idx)), v)
+        with pytest.raises(mb.MidbfError) as e:
+            mb.Phase.recover(X, W, rows, cols, r=2, q=2)
+        assert e.value.code == mb.ECALLBACK
 
 
 def test_recovery_partitions_at_a_jump():
