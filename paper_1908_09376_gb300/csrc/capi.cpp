@@ -148,6 +148,14 @@ int midbf_build(const midbf_phase* ph, const midbf_params* p, midbf_plan** out) 
         if (!ph || !p || !out) fail(MIDBF_EINVAL, "null argument");
         if (!(p->tol > 0.0 && p->tol < 1.0)) fail(MIDBF_EINVAL, "tol must be in (0, 1)");
         if (p->n0 <= 0 || !(p->t >= 1.0) || p->kest <= 0 || p->kmax < 0) fail(MIDBF_EINVAL, "bad parameters");
+        if (p->use_box) {
+            const int d = as_phase(ph)->d;
+            for (const double* box : {p->boxX, p->boxW}) {
+                for (int k = 0; k < d; ++k)
+                    if (!std::isfinite(box[k])) fail(MIDBF_EINVAL, "non-finite box corner");
+                if (!(std::isfinite(box[d]) && box[d] > 0.0)) fail(MIDBF_EINVAL, "box side must be positive");
+            }
+        }
         auto pl = build_plan(*as_phase(ph), *p);
         *out = reinterpret_cast<midbf_plan*>(pl.release());
     });

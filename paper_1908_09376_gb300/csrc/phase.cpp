@@ -174,6 +174,10 @@ void phase_check(const Phase& ph) {
         default:
             fail(MIDBF_EINVAL, "unknown phase family " + std::to_string(ph.family));
     }
+    for (double v : ph.U)
+        if (!std::isfinite(v)) fail(MIDBF_EINVAL, "non-finite low-rank factor U");
+    for (double v : ph.V)
+        if (!std::isfinite(v)) fail(MIDBF_EINVAL, "non-finite low-rank factor V");
     for (double v : ph.X)
         if (!std::isfinite(v)) fail(MIDBF_EINVAL, "non-finite coordinate in X");
     for (double v : ph.W)

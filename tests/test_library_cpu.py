@@ -152,6 +152,16 @@ def test_malformed_input_rejected():
     with pytest.raises(mb.MidbfError) as e:
         mb.Phase.closed_form(99, X, W)
     assert e.value.code == mb.EINVAL
+    U = np.ones((X.shape[0], 2))
+    U[3, 1] = np.nan
+    with pytest.raises(mb.MidbfError) as e:
+        mb.Phase.lowrank(X, W, U, np.ones((W.shape[0], 2)))
+    assert e.value.code == mb.EINVAL
+    ph = mb.Phase.closed_form(synth.PHASE_FIO2D, X, W)
+    for box in ((np.zeros(2), 0.0), (np.zeros(2), float("nan")), (np.array([0.0, np.inf]), 1.0)):
+        with pytest.raises(mb.MidbfError) as e:
+            mb.Plan.build(ph, tol=1e-6, n0=16, boxX=box, boxW=bw)
+        assert e.value.code == mb.EINVAL
     plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16, boxX=bx, boxW=bw)
     data = bytearray(plan.export())
     with pytest.raises(mb.MidbfError) as e:
