@@ -56,11 +56,23 @@ def parse():
     ap.add_argument("--n", type=int, default=None, help="grid size of the 2D workloads")
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--skip-extras", action="store_true", help="only the headline measurement")
+    ap.add_argument("--sweep", default=None,
+                    help="comma-separated grid sizes n: the one-RHS FP32 apply of the FIO2D plan family at each "
+                         "(the scaling of Fig. 8), with build times; prints one JSON line with a 'sweep' list")
+    ap.add_argument("--cpu-sample-every", type=int, default=32,
+                    help="the CPU oracle times every k-th block of every stage and scales by the entry ratio "
+                         "(1: the whole apply)")
     ap.add_argument("--workload", default="fio2d",
-                    choices=["fio2d", "fio3d_n32", "fio2d_jump", "batched", "nuft3d", "helmholtz"],
+                    choices=["fio2d", "fio3d_n32", "fio2d_jump", "batched", "nuft3d", "nuft3d_recovered",
+                             "fio2d_paper", "helmholtz"],
                     help="fio2d: 2D FIO phase on the n x n grid (--n, default 256); fio3d_n32: 3D, N = 32,768, "
                          "random X; fio2d_jump: 2D with the jump |xi| sign(x1 - 1/2) (--n, default 1024); "
-                         "nuft3d: Example 2, N = n^3 random points (--n, default 64); helmholtz: Example 3 on "
+                         "nuft3d: Example 2, N = n^3 random points (--n, default 64); nuft3d_recovered: the same "
+                         "with the phase recovered from 8 rows and 8 columns of K (Scenario 2, Algorithm 7, "
+                         "r = 4, q = 2) and the middle factor made from the low-rank phase; fio2d_paper: Example 1 "
+                         "as the paper discretizes it (X and Omega the n x n grid in [0,1)^2, --n default 1024), "
+                         "the phase recovered with r = 10, q = 2, ID tolerance 1e-9 (Table 2's setting); "
+                         "helmholtz: Example 3 on "
                          "the sphere mesh of refinement level --n (default 6: 20,609 x 20,353 points)")
     ap.add_argument("--nrhs", type=int, default=None, help="right-hand sides (default: the workload's)")
     ap.add_argument("--mode", default=None, choices=["fp32", "bf16", "bf16r"],
@@ -111,12 +123,17 @@ def pick_workload(args):
         n = args.n or base.n
         w = synth.Workload(f"fio2d_jump_n{n}", 2, n, base.phase, base.tol, base.n0, base.nrhs, base.f_seed,
                            sample_rows=base.sample_rows, sample_seed=base.sample_seed)
-    elif args.workload == "nuft3d":
+    elif args.workload in ("nuft3d", "nuft3d_recovered"):
         base = synth.WORKLOADS["nuft3d_n64"]
         n = args.n or base.n
-        w = synth.Workload(f"nuft3d_n{n}", 3, n, base.phase, base.tol, base.n0, 1, base.f_seed,
-                           x_kind="random", x_seed=base.x_seed, w_kind="random", w_seed=base.w_seed,
-                           sample_rows=256, sample_seed=3)
+        rec = args.workload == "nuft3d_recovered"
+        w = synth.Workload(f"nuft3d_n{n}" + ("_recovered" if rec else ""), 3, n, base.phase, base.tol, base.n0, 1,
+                           base.f_seed, x_kind="random", x_seed=base.x_seed, w_kind="random", w_seed=base.w_seed,
+                           sample_rows=256, sample_seed=3, recovered=rec)
+    elif args.workload == "fio2d_paper":
+        n = args.n or 1024
+        w = synth.Workload(f"fio2d_paper_n{n}", 2, n, synth.PHASE_FIO2D, 1e-9, 64, 1, 0, w_kind="unit",
+                           recovered=True, sample_rows=256, sample_seed=3, t=5.0)
     elif args.workload == "helmholtz":
         base = synth.WORKLOADS["helmholtz_l6"]
         lev = args.n or base.n
@@ -133,6 +150,9 @@ def pick_workload(args):
     graph = (args.graph or ("on" if jump else "off")) == "on"
     return w, nrhs, mode, build, store, tune, graph
 
+
+# Table 2 of the paper: T_app (s) for Example 1 at n = 16 ... 4096 with r = 10, k = 30.
+TABLE2_T_APP = {16: 2.81e-4, 64: 4.43e-3, 256: 4.00e-2, 1024: 6.86e-1, 4096: 1.64e1}
 
 PHASE_NAMES = {synth.PHASE_FIO2D: "FIO2D closed form", synth.PHASE_FIO3D: "FIO3D closed form",
                synth.PHASE_FIO2D_JUMP: "FIO2D + jump closed form", synth.PHASE_DOT: "x.xi closed form",
@@ -251,7 +271,10 @@ class OracleSample:
         from oracle import midbf as omidbf
         from oracle import planio
         fac = planio.read(plan_bytes)
-        self.cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+        # the oracle's apply is a chain of scipy CSR products, which run on one
+        # thread whatever the core count (no BLAS call is involved)
+        self.cores = 1
+        self.host_cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
         rng = np.random.default_rng(0)
         self.parts = []
         sampled = total = 0
@@ -269,8 +292,11 @@ class OracleSample:
             sampled += sum(ent[i] for i in pick)
             in_len = st.out_len
         self.scale = total / max(1, sampled)
-        self.desc = (f"every {sample_every}th block of each stage ({sampled} of {total} factor entries); "
-                     f"forward+adjoint sparse FP64 apply of {nrhs} RHS; time scaled by the entry ratio")
+        what = ("every block (the whole apply)" if sample_every == 1 else
+                f"every {sample_every}th block of each stage ({sampled} of {total} factor entries)")
+        self.desc = (f"{what}; forward+adjoint sparse FP64 apply of {nrhs} RHS (scipy CSR products, one thread, "
+                     f"{self.host_cores} host cores present)" +
+                     ("" if sample_every == 1 else "; time scaled by the entry ratio"))
 
     def step_seconds(self):
         t0 = time.perf_counter()
@@ -280,9 +306,9 @@ class OracleSample:
         return (time.perf_counter() - t0) * self.scale
 
 
-def cpu_baseline(plan_bytes, n_points, seconds_budget=15.0, nrhs=1):
+def cpu_baseline(plan_bytes, n_points, seconds_budget=15.0, nrhs=1, sample_every=32):
     """n_points: outputs of one forward + adjoint step per RHS (|X| + |Omega|)."""
-    smp = OracleSample(plan_bytes, nrhs=nrhs)
+    smp = OracleSample(plan_bytes, sample_every=sample_every, nrhs=nrhs)
     times = []
     t0 = time.perf_counter()
     while time.perf_counter() - t0 < seconds_budget or len(times) < 3:
@@ -297,9 +323,11 @@ def run_reference(args, ws, rank):
     on this arm's workload (its plan built by the library on the host)."""
     if rank != 0:
         return
-    if args.workload in ("batched", "fio2d_jump"):
-        why = ("32 plans built on the GPU" if args.workload == "batched" else
-               "the n = 1024 plan (1.6e10 T entries) is built on the GPU and does not fit the host twice")
+    if args.workload in ("batched", "fio2d_jump", "nuft3d_recovered"):
+        why = {"batched": "32 plans built on the GPU",
+               "fio2d_jump": "the n = 1024 plan (1.6e10 T entries) is built on the GPU and does not fit the host twice",
+               "nuft3d_recovered": "its phase is recovered with the GPU's Algorithm 4 (--workload nuft3d times the "
+                                   "oracle on the closed-form plan of the same points)"}[args.workload]
         print(json.dumps({"impl": "reference", "unavailable": f"oracle arm not run for {args.workload}: {why}"}),
               flush=True)
         return
@@ -308,7 +336,7 @@ def run_reference(args, ws, rank):
     X, W, bx, bw = wl.points()
     plan = mb.Plan.build(mb.Phase.closed_form(wl.phase, X, W), tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw,
                          nthreads=args.threads, t=wl.t)
-    smp = OracleSample(plan.export(), nrhs=R1)
+    smp = OracleSample(plan.export(), sample_every=max(1, args.cpu_sample_every), nrhs=R1)
     del plan
     units = (wl.nx + wl.nw) * R1
     for _ in range(args.warmup):
@@ -466,11 +494,91 @@ def main_batched(args, ws, rank, dev, pg):
         print(json.dumps(out), flush=True)
 
 
+def main_sweep(args, ws, rank, dev, pg):
+    """Fig. 8's scaling in N: the FIO2D family (Example 1's phase on the n x n
+    grid, ID tolerance 1e-6, n0 = 64) at each n of --sweep, one RHS, FP32,
+    forward + adjoint per step, L2 flushed between steps; with the build, the
+    upload and the sampled rel-L2 against FP64 direct sums beside each n."""
+    import torch
+    import paper_1908_09376_gb300 as mb
+    ns = [int(v) for v in args.sweep.split(",") if v.strip()]
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    rows_out = []
+    launches = 0
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for n in ns:
+        w = synth.Workload(f"fio2d_n{n}", 2, n, synth.PHASE_FIO2D, 1e-6, 64, 1, 0, sample_rows=256, sample_seed=3)
+        X, W, bx, bw = w.points()
+        ph = mb.Phase.closed_form(w.phase, X, W)
+        dev_ids = n >= 512          # the host QRs of the large plans take too long
+        t0 = time.perf_counter()
+        plan = mb.Plan.build(ph, tol=w.tol, n0=w.n0, boxX=bx, boxW=bw, nthreads=args.threads,
+                             device_ids=1 if dev_ids else 0, store_fp32=1 if n >= 1024 else 0)
+        t_build = time.perf_counter() - t0
+        st = plan.stats()
+        t0 = time.perf_counter()
+        dp = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY, consume=True)
+        t_up = time.perf_counter() - t0
+        del plan
+        fbytes, ibytes = dp.bytes()
+        N = w.N
+        f_host = synth.complex_gaussian(N, 1, w.f_seed)
+        f = torch.from_numpy(f_host[:, 0].copy()).to(dev, torch.complex64)
+        g = torch.empty(N, dtype=torch.complex64, device=dev)
+        h = torch.empty(N, dtype=torch.complex64, device=dev)
+        wsb = torch.empty(dp.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        for _ in range(max(3, args.warmup)):
+            dp.apply(f, out=g, workspace=wsb)
+            dp.apply(g, adjoint=True, out=h, workspace=wsb)
+        torch.cuda.synchronize()
+        launches += args.steps * 2 * dp.launches(1)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            dp.apply(f, out=g, workspace=wsb)
+            dp.apply(g, adjoint=True, out=h, workspace=wsb)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        rws = synth.sample_rows(N, 256, 3)
+        e_f, e_a = sampled_direct_error(ph, f_host.T, g.reshape(1, N).cpu().numpy(), g.reshape(1, N).cpu().numpy(),
+                                        h.reshape(1, N).cpu().numpy(), rws, synth.sample_rows(N, 256, 4))
+        rows_out.append({"n": n, "N": N, "L": st["L"], "t_entries": st["t_entries"], "s_entries": st["s_entries"],
+                         "mean_rank": round(st["mean_rank"], 1), "max_rank": st["max_rank"],
+                         "build": "device IDs" if dev_ids else "host", "build_s": round(t_build, 1),
+                         "upload_s": round(t_up, 1), "ms_per_step": round(ms, 4),
+                         "points_rhs_per_s": 2 * N / (ms * 1e-3),
+                         "factor_GBps": round((fbytes + ibytes) * 2 / (ms * 1e-3) / 1e9, 1),
+                         "rel_l2_direct_sampled": {"forward": e_f, "adjoint": e_a}})
+        log(f"sweep n={n}: {rows_out[-1]}")
+        del dp, wsb, f, g, h
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    last = rows_out[-1]
+    out = {"metric": METRIC, "value": last["points_rhs_per_s"] * ws, "unit": "points*RHS/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": last["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": "fio2d_sweep", "ns": ns, "nrhs": 1, "mode": "fp32", "tol": 1e-6, "n0": 64,
+                      "step": "forward + adjoint apply", "l2": "flushed (512 MB write) between timed steps",
+                      "value_at": f"n = {last['n']}", "parallelism": f"replicas x{ws}"},
+           "sweep": rows_out, "clocks": clk, "gpu_launches": launches, "cpu_baseline": None}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.sweep:
+        import torch
+        torch.cuda.set_device(local)
+        main_sweep(args, ws, rank, torch.device("cuda", local), None)
         return
     if args.workload == "batched":
         import torch
@@ -501,7 +609,39 @@ def main():
     X, W, bx, bw = wl.points()
 
     t0 = time.perf_counter()
-    ph = mb.Phase.closed_form(wl.phase, X, W)
+    recovery = None
+    ph_true = mb.Phase.closed_form(wl.phase, X, W)
+    if wl.recovered:
+        # Scenario 2 (Table 1): the phase is not known; Algorithm 7 recovers a rank-r
+        # phase from r q rows and r q columns of K (plus those added for
+        # discontinuities), with every vector recovery (Algorithm 4) on the GPU.  The
+        # rows and columns of K come from the library's FP64 evaluation of the phase.
+        r_rec = 10 if args.workload == "fio2d_paper" else 4
+
+        def k_rows(idx):
+            ix = np.repeat(idx, nw)
+            iw = np.tile(np.arange(nw, dtype=np.int64), len(idx))
+            return np.exp(2j * np.pi * ph_true.eval(ix, iw)).reshape(len(idx), nw)
+
+        def k_cols(idx):
+            ix = np.tile(np.arange(nx, dtype=np.int64), len(idx))
+            iw = np.repeat(idx, nx)
+            return np.exp(2j * np.pi * ph_true.eval(ix, iw)).reshape(len(idx), nx).T
+
+        ph = mb.Phase.recover(X, W, k_rows, k_cols, r=r_rec, q=2, seed=0, device=True)
+        t_rec = time.perf_counter() - t0
+        # eps^K of Sec. 4 on 256 sampled indices: recovered against the true phase
+        S = synth.sample_rows(min(nx, nw), 256, 7)
+        Ur, Vr = ph.factors()
+        A = np.exp(2j * np.pi * ph_true.eval(np.repeat(S, len(S)), np.tile(S, len(S)))).reshape(len(S), len(S))
+        B = np.exp(2j * np.pi * (Ur[S] @ Vr[S].T))
+        eps_k = float(np.linalg.norm(A - B, 2) / np.linalg.norm(A, 2))
+        recovery = {"r": r_rec, "q": 2, "device_unwrap": True, "recover_s": round(t_rec, 2), "eps_K": eps_k,
+                    **{k: (float(v) if k == "tau" else int(v)) for k, v in ph.info.items()}}
+        log(f"phase recovered: eps_K {eps_k:.2e}, {ph.info}")
+        t0 = time.perf_counter()
+    else:
+        ph = ph_true
     plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads, t=wl.t,
                          device_ids=1 if build_site == "device" else 0, store_fp32=1 if store == "fp32" else 0)
     t_build = time.perf_counter() - t0
@@ -511,13 +651,17 @@ def main():
     log(f"built {wl.name}: {st['t_entries']} T entries, {st['s_entries']} S entries")
     t0 = time.perf_counter()
     mode = {"fp32": mb.FP32, "bf16": mb.BF16, "bf16r": mb.BF16 | mb.REFINE}[mode_name]
-    keep_plan = args.workload == "fio2d" and not args.skip_extras and R1 == 1
+    keep_plan = args.workload in ("fio2d", "fio2d_paper") and not args.skip_extras and R1 == 1
+    # the on-the-fly middle factor takes at most 8 low-rank phase terms; a rank-10
+    # recovered phase runs with the middle factor stored
+    s_mode_main = mb.S_STORED if (wl.recovered and recovery and recovery["r"] > 8) else mb.S_ONTHEFLY
     # the oracle's baseline needs the plan file; the small workloads export it before the upload
     # consumes the host copy (the n = 1024 plan is too large to hold twice)
-    want_cpu = rank == 0 and ws == 1 and not args.skip_extras and args.workload not in ("fio2d_jump",)
+    want_cpu = rank == 0 and ws == 1 and not args.skip_extras and args.workload not in ("fio2d_jump",
+                                                                                         "nuft3d_recovered")
     plan_bytes = plan.export() if want_cpu and not keep_plan else None
     # large plans: hand the coefficients to the device as they are uploaded
-    dp32 = mb.DevicePlan(plan, mode, mb.S_ONTHEFLY, consume=not keep_plan)
+    dp32 = mb.DevicePlan(plan, mode, s_mode_main, consume=not keep_plan)
     t_up = time.perf_counter() - t0
     log("device plan uploaded")
     if not keep_plan:
@@ -621,8 +765,11 @@ def main():
             row["TFLOPs"] = round(stage_flops(k[0], k[1]) / (ms_ * 1e-3) / 1e12, 1)
         stage_rows.append(row)
     # the middle factor made on the fly with the SIMT kernels is bound by the SFU: every
-    # entry needs one sine and one cosine, 16 SFU operations per clock per SM
-    sfu_peak = 152 * 16 * 2.07e9 / 2 / 1e9          # G entries/s at the maximum SM clock
+    # entry needs one sine and one cosine, and for the phases with a square-root term one
+    # reciprocal square root; the SFU completes 16 operations per clock per SM
+    sfu_ops = 3 if wl.phase in (synth.PHASE_FIO2D, synth.PHASE_FIO3D, synth.PHASE_FIO2D_JUMP,
+                                synth.PHASE_DISTANCE) and not wl.recovered else 2
+    sfu_peak = 152 * 16 * 2.07e9 / sfu_ops / 1e9    # G entries/s at the maximum SM clock
     s_entries_of = {q_: sinfo[q_][1] for q_ in range(ns) if sinfo[q_][0] == 1}
 
     def hbm_roofline(exclude_s):
@@ -648,7 +795,8 @@ def main():
         roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(sfu_peak, 1), "unit": "Gentries/s",
                     "frac": round(achieved / sfu_peak, 4), "traffic": None,
                     "kernel": f"{direction} stage {q} (S, made on the fly)",
-                    "peak_source": "derived: 152 SMs x 16 SFU ops/clk x 2.07 GHz / 2 (one sine, one cosine per entry)"}
+                    "peak_source": (f"derived: 152 SMs x 16 SFU ops/clk x 2.07 GHz / {sfu_ops} (SFU operations per "
+                                    "entry: sine, cosine" + (", reciprocal square root)" if sfu_ops == 3 else ")"))}
         roofline_hbm = hbm_roofline(True)
         roofline_hbm["whole_step_GBps"] = round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1)
     else:
@@ -671,8 +819,57 @@ def main():
         e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Gn, Hn, rows, cols)
         acc = {"forward": e_f, "adjoint": e_a, "rows": int(wl.sample_rows),
                "reference": "FP64 direct sum over all columns (rows) for sampled outputs"}
+        if wl.recovered:
+            # end to end: against eq. (1) with the true phase (the recovered phase only
+            # fixes K up to integers in Psi, which exp(2 pi i .) does not see)
+            t_f, t_a = sampled_direct_error(ph_true, f_host.T, Gn, Gn, Hn, rows, cols)
+            acc["forward_vs_true_phase"] = t_f
+            acc["adjoint_vs_true_phase"] = t_a
+            acc["reference"] += "; Phi = the recovered low-rank phase (*_vs_true_phase: the closed form)"
 
     extras = {}
+    vs_baseline = None
+    if args.workload == "fio2d_paper":
+        # Table 2 (n, r = 10, k = 30): T_app of the paper's MATLAB code on one 3.2 GHz core,
+        # presumably FP64; points/s = N / T_app for one direction, the per-direction rate
+        # that value also measures (context: another machine and precision)
+        t_app = TABLE2_T_APP.get(n)
+        if t_app:
+            extras["paper_table2"] = {"T_app_s": t_app, "points_per_s": N / t_app, "hardware": "MATLAB, 1 thread, 3.2 GHz",
+                                      "row": f"n = {n}, r = 10, k = 30"}
+            vs_baseline = value / (N / t_app)
+    if not args.skip_extras and R1 == 1 and args.workload == "fio2d_paper":
+        # the plain FP64 form of the same recovered factors (the paper's precision)
+        dp64 = mb.DevicePlan(plan, mb.FP64, mb.S_STORED)
+        f64 = f.to(torch.complex128)
+        g64 = torch.empty(N, dtype=torch.complex128, device=dev)
+        h64 = torch.empty(N, dtype=torch.complex128, device=dev)
+        ws64 = torch.empty(dp64.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            dp64.apply(f64, out=g64, workspace=ws64)
+            dp64.apply(g64, adjoint=True, out=h64, workspace=ws64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot64 = 0.0
+        k64 = max(3, args.steps // 2)
+        for _ in range(k64):
+            flush.zero_()
+            e0.record(stream)
+            dp64.apply(f64, out=g64, workspace=ws64)
+            dp64.apply(g64, adjoint=True, out=h64, workspace=ws64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot64 += e0.elapsed_time(e1)
+        ms64 = tot64 / k64
+        G64 = g64.reshape(1, N).cpu().numpy()
+        H64 = h64.reshape(1, N).cpu().numpy()
+        rws = synth.sample_rows(N, 256, wl.sample_seed)
+        cls = synth.sample_rows(N, 256, wl.sample_seed + 1)
+        e_f, e_a = sampled_direct_error(ph_true, f_host.T, G64, G64, H64, rws, cls)
+        extras["plain_fp64"] = {"value": 2 * N / (ms64 * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(ms64, 4),
+                                "s_mode": "stored", "rel_l2_vs_true_phase": {"forward": e_f, "adjoint": e_a},
+                                "vs_paper_table2": (2 * N / (ms64 * 1e-3)) / (N / t_app) if t_app else None}
+        del dp64, ws64
     if not args.skip_extras and R1 == 1 and args.workload == "fio2d":
         # plain FP64 form (middle factor stored: FP64 sincospi on GB300 is slow)
         dp64 = mb.DevicePlan(plan, mb.FP64, mb.S_STORED)
@@ -728,40 +925,69 @@ def main():
             totR += e0.elapsed_time(e1)
         msR = totR / kR
         extras["nrhs64_fp32"] = {"value": 2 * N * R / (msR * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msR, 3)}
-        # the same with the middle factor on the tensor cores (BF16 + refinement)
-        dptc = mb.DevicePlan(plan, mb.BF16 | mb.REFINE, mb.S_ONTHEFLY)
-        Gt = torch.empty((R, N), dtype=torch.complex64, device=dev)
-        Ht = torch.empty((R, N), dtype=torch.complex64, device=dev)
+        # the same with every stage on the tensor cores (BF16 + refinement), at 64 and
+        # at 256 RHS (one full pass of the TMEM accumulator); forward and adjoint each
+        # timed, and per stage: algorithmic flops (8 per complex multiply-add of the
+        # method's factor entries per RHS) and issued flops (3 products refined, over
+        # the dense blocks that the tensor cores multiply, identity parts included)
         del wsR
-        wsR = torch.empty(dptc.workspace_bytes(R), dtype=torch.uint8, device=dev)   # with the RHS-image area
-        dptc.apply(F, out=Gt, workspace=wsR)
-        torch.cuda.synchronize()
-        totT = 0.0
-        dptc.profile(True)
-        s_ms = []
-        for _ in range(kR):
-            flush.zero_()
-            e0.record(stream)
+        dptc = mb.DevicePlan(plan, mb.BF16 | mb.REFINE, mb.S_ONTHEFLY)
+        Gref = G
+        for R in (64, 256):
+            F = torch.from_numpy(synth.complex_gaussian(N, R, 0).T.copy()).to(dev, torch.complex64)
+            if R != 64:
+                Gref = torch.empty((R, N), dtype=torch.complex64, device=dev)
+                ws32 = torch.empty(dp32.workspace_bytes(R), dtype=torch.uint8, device=dev)
+                dp32.apply(F, out=Gref, workspace=ws32)
+                del ws32
+            Gt = torch.empty((R, N), dtype=torch.complex64, device=dev)
+            Ht = torch.empty((R, N), dtype=torch.complex64, device=dev)
+            wsR = torch.empty(dptc.workspace_bytes(R), dtype=torch.uint8, device=dev)   # with the RHS-image area
             dptc.apply(F, out=Gt, workspace=wsR)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            totT += e0.elapsed_time(e1)
-            s_ms += [ms for kind, ms, by in dptc.stage_times() if kind == 1]
             dptc.apply(Gt, adjoint=True, out=Ht, workspace=wsR)
             torch.cuda.synchronize()
-            s_ms += [ms for kind, ms, by in dptc.stage_times() if kind == 1]
-        dptc.profile(False)
-        msT = totT / kR * 2   # forward measured alone, adjoint assumed equal in the ratio
-        rel_tc = (torch.linalg.vector_norm(Gt - G) / torch.linalg.vector_norm(G)).item()
-        s_entries = st["s_entries"]
-        s_ms_mean = statistics.mean(s_ms) if s_ms else float("nan")
-        tc_tflops = 3 * 8.0 * s_entries * R / (s_ms_mean * 1e-3) / 1e12
-        extras["nrhs64_bf16_refine"] = {
-            "fwd_ms": round(totT / kR, 3), "s_stage_ms": round(s_ms_mean, 4),
-            "s_stage_issued_TFLOPs": round(tc_tflops, 1),
-            "s_stage_tensor_frac_of_bf16_dense_peak": round(tc_tflops * 1e12 / (PEAK_BF16 * 1e12), 4),
-            "rel_l2_vs_fp32": rel_tc, "status": dptc.status()}
-        del wsR, F, G, H, Gt, Ht, dptc
+            tf = ta = 0.0
+            for _ in range(kR):
+                flush.zero_()
+                e0.record(stream)
+                dptc.apply(F, out=Gt, workspace=wsR)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tf += e0.elapsed_time(e1)
+                flush.zero_()
+                e0.record(stream)
+                dptc.apply(Gt, adjoint=True, out=Ht, workspace=wsR)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ta += e0.elapsed_time(e1)
+            dptc.profile(True)
+            srows = {}
+            for adj_ in (False, True):
+                flush.zero_()
+                dptc.apply(Gt if adj_ else F, adjoint=adj_, out=Ht if adj_ else Gt, workspace=wsR)
+                for q_, (kind_, ms_, _) in enumerate(dptc.stage_times()):
+                    sidx = ns - 1 - q_ if adj_ else q_
+                    alg = 8.0 * sinfo[sidx][1] * R / (ms_ * 1e-3) / 1e12
+                    iss = 3 * 8.0 * (sinfo[sidx][2] if kind_ != 1 else sinfo[sidx][1]) * R / (ms_ * 1e-3) / 1e12
+                    srows.setdefault((q_, kind_), []).append((ms_, alg, iss))
+            dptc.profile(False)
+            s_rows = [v for (q_, k_), v in srows.items() if k_ == 1][0]
+            vu = max(((q_, k_, v) for (q_, k_), v in srows.items() if k_ != 1), key=lambda t: sum(x[0] for x in t[2]))
+            rel_tc = (torch.linalg.vector_norm(Gt - Gref) / torch.linalg.vector_norm(Gref)).item()
+            msT = (tf + ta) / kR
+            extras[f"nrhs{R}_bf16_refine"] = {
+                "value": 2 * N * R / (msT * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msT, 3),
+                "fwd_ms": round(tf / kR, 3), "adj_ms": round(ta / kR, 3),
+                "s_stage_ms": [round(x[0], 4) for x in s_rows],
+                "s_stage_TFLOPs_algorithmic": [round(x[1], 1) for x in s_rows],
+                "s_stage_TFLOPs_issued": [round(x[2], 1) for x in s_rows],
+                "s_stage_issued_frac_of_bf16_peak": [round(x[2] / PEAK_BF16, 4) for x in s_rows],
+                "largest_vu_stage": {"stage": vu[0], "kind": "VSU"[vu[1]], "ms": [round(x[0], 4) for x in vu[2]],
+                                     "TFLOPs_issued": [round(x[2], 1) for x in vu[2]]},
+                "peak_TFLOPs": PEAK_BF16, "peak_source": PEAK_BF16_SOURCE,
+                "rel_l2_vs_fp32": rel_tc, "status": dptc.status()}
+            del wsR, F, Gt, Ht
+        del G, H, Gref, dptc
 
     # end to end through the host-buffer entry point (pinned host memory)
     fh = torch.from_numpy(f_host.T.astype(np.complex64).copy()).pin_memory()
@@ -786,15 +1012,21 @@ def main():
     cpu = None
     if want_cpu:
         try:
-            cpu = cpu_baseline(plan_bytes if plan_bytes is not None else plan.export(), nx + nw, nrhs=R1)
+            cpu = cpu_baseline(plan_bytes if plan_bytes is not None else plan.export(), nx + nw, nrhs=R1,
+                               sample_every=max(1, args.cpu_sample_every))
         except Exception as e:  # the GPU numbers stand without it
             cpu = {"error": f"{type(e).__name__}: {e}"}
 
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": vs_baseline, "dtype": "c64", "data": "synthetic",
            "config": {"workload": wl.name, "N": N, "nx": nx, "nw": nw, "d": wl.d,
-                      "phase": PHASE_NAMES.get(wl.phase, str(wl.phase)),
+                      "phase": (f"{PHASE_NAMES.get(wl.phase, str(wl.phase)).replace(' closed form', '')} recovered "
+                                f"from {2 * recovery['r']} rows + {2 * recovery['r']} columns of K (Algorithm 7, "
+                                f"r = {recovery['r']}, q = 2): low-rank UV^T" if wl.recovered
+                                else PHASE_NAMES.get(wl.phase, str(wl.phase))),
+                      "omega": wl.w_kind, "s_mode": "stored" if s_mode_main == mb.S_STORED else "on the fly",
+                      "recovery": recovery,
                       "points": wl.x_kind, "nrhs": R1, "mode": mode_name, "step": "forward + adjoint apply",
                       "tol": wl.tol, "n0": wl.n0, "L": st["L"], "build": build_site, "store": store,
                       "autotuned": tune, "tune_s": round(t_tune, 1), "cuda_graph": use_graph,

@@ -130,6 +130,55 @@ int midbf_phase_recover(int d, int64_t nx, const double* X, int64_t nw, const do
                         const midbf_access* acc, int r, int q, double tau, int max_disc,
                         uint64_t seed, midbf_phase** out, midbf_recover_info* info);
 
+/* midbf_phase_recover with flags.  MIDBF_RECOVER_DEVICE: every vector
+ * recovery of Algorithm 4 - the detection of discontinuities along the root
+ * column and root row, and the recovery of the sampled rows and columns
+ * along each piece of Algorithm 6 - runs on the current CUDA device
+ * (midbf_recover_vectors); the recovery paths (Algorithm 5) and the
+ * factorization (Algorithm 1) stay on the host.  The result is the same bit
+ * for bit as with flags = 0.  Errors as midbf_phase_recover, MIDBF_EINVAL for
+ * unknown flags, and MIDBF_ECUDA / MIDBF_ENOMEM from the device. */
+#define MIDBF_RECOVER_DEVICE 1
+int midbf_phase_recover_ex(int d, int64_t nx, const double* X, int64_t nw, const double* W,
+                           const midbf_access* acc, int r, int q, double tau, int max_disc,
+                           uint64_t seed, int flags, midbf_phase** out, midbf_recover_info* info);
+
+/* ---- vector recovery on the GPU (Algorithm 4, Sec. 2.3) -------------------
+ * Algorithm 4 fixes, along a recovery path (Def. 3.3), the unwrapped value of
+ * each child from its parent's, v(ed) = u(ed) - round(u(ed) - v(bg)) (round
+ * half away from zero), and flags ed when |v(ed) - v(bg)| >= tau; D is the
+ * path root followed by the flagged children in path order.
+ *
+ * midbf_rpath_create: a path (or a piece of one, as Partition2 cuts it) over
+ * n points, on the current device.  edges: nedges (parent, child) pairs,
+ * row-major int64, host memory, copied; every parent must be root or the
+ * child of an earlier edge, and no node may be a child twice.  The edges are
+ * cut into runs of consecutive edges whose parents were all fixed by earlier
+ * runs (one run per depth for a breadth-first path); midbf_rpath_info reports
+ * their number.  Errors: MIDBF_EINVAL (bad sizes or edges, n >= 2^31),
+ * MIDBF_ECUDA (no device), MIDBF_ENOMEM. */
+typedef struct midbf_rpath midbf_rpath;
+int midbf_rpath_create(int64_t n, int64_t nedges, const int64_t* edges, int64_t root, midbf_rpath** out);
+void midbf_rpath_destroy(midbf_rpath* p);
+int midbf_rpath_info(const midbf_rpath* p, int64_t* n, int64_t* nedges, int* nruns);
+
+/* midbf_recover_vectors: Algorithm 4 along the path for nvec vectors at once
+ * (one CTA per vector, the runs one after the other), asynchronous on stream
+ * (a cudaStream_t).  Device arrays: u (nvec x n, leading dimension ldu) the
+ * observed values modulo one; v (ldv) holds the start values (at least at the
+ * root) on entry and the recovered values on exit (entries not reached by
+ * the edges keep their start values); u and v must not overlap.  flags
+ * (optional, uint8, nvec x nedges, ldf): 1 where the edge's child is flagged
+ * at tau.  D (optional, needs flags; int64, ldD >= nedges + 1) and nD
+ * (optional, int64 per vector): the flagged set D of each vector and its
+ * length.  Every edge performs the FP64 operations of the sequential loop,
+ * so v, flags and D equal a sequential run of Algorithm 4 bit for bit.
+ * Errors: MIDBF_EINVAL (bad arguments, or the current device is not the
+ * path's), MIDBF_ECUDA. */
+int midbf_recover_vectors(const midbf_rpath* p, int nvec, const double* u, int64_t ldu, double* v, int64_t ldv,
+                          double tau, uint8_t* flags, int64_t ldf, int64_t* D, int64_t ldD, int64_t* nD,
+                          void* stream);
+
 /* Evaluate Phi at n index pairs (ix[c], iw[c]) into out[c] (host, FP64). */
 int midbf_phase_eval(const midbf_phase* ph, int64_t n, const int64_t* ix, const int64_t* iw,
                      double* out);
@@ -246,8 +295,12 @@ int midbf_workspace_size(const midbf_dplan* dp, int nrhs, size_t* bytes);
 int midbf_dplan_bytes(const midbf_dplan* dp, size_t* factor_bytes, size_t* index_bytes);
 
 /* midbf_apply: out = K in (adjoint = 0; in has nw entries, out nx) or
- * out = K^H in (adjoint = 1; in nx, out nw), for nrhs right-hand sides, on
- * the CUDA stream `stream` (cudaStream_t, NULL = legacy default stream).
+ * out = K^H in (adjoint = 1; in nx, out nw), for nrhs right-hand sides.  The
+ * forward apply is the factor product of eq. (finishIDBF) (Sec. 3.5),
+ * U^L ... U^h S^h V^h ... V^L applied right to left to f, which approximates
+ * the sum g(x_i) = sum_j exp(2 pi i Phi(x_i, xi_j)) f(xi_j) of eq. (1); the
+ * adjoint applies the conjugate transposes of the same factors in reverse
+ * order, (V^L)^H ... (S^h)^H ... (U^L)^H.  Runs on the CUDA stream `stream` (cudaStream_t, NULL = legacy default stream).
  * in/out are device pointers with leading dimensions ldin/ldout (>= vector
  * length); they must not overlap.  workspace: device memory of at least
  * midbf_workspace_size bytes, owned by the caller, not shared between calls
@@ -286,9 +339,32 @@ int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adj
                         const int64_t* ldout, const int* nrhs, void* stream,
                         void* workspace, size_t workspace_bytes);
 
+/* ---- overlap of the middle factor with its neighbouring stage ------------
+ * The middle factor S (Sec. 3.5) is bound by arithmetic (its entries are
+ * made on the fly), the U stage after it by memory.  Each U block reads the
+ * outputs of a few S blocks only, and these blocks fall into independent
+ * groups; midbf_dplan_create deals the groups into (up to 4) chunks.  With
+ * the overlap on (the default when a plan has at least two groups), an apply
+ * on the SIMT kernels runs S and that U stage chunk by chunk: forward, chunk
+ * k of S on the caller's stream and chunk k of U, after an event, on a side
+ * stream of the plan; adjoint, U's adjoint chunk first and S's adjoint chunk
+ * on the side stream.  The side stream forks from the caller's stream before
+ * the pair and joins it after, so the apply stays ordered on the caller's
+ * stream and can be recorded into a graph.  Results are the same bit for bit
+ * as with the overlap off.  The overlap is skipped while profiling is on
+ * (midbf_dplan_profile times each stage alone) and for stages on the tensor
+ * cores.  Applies of one plan from several host threads are serialized while
+ * they issue the overlapped pair.  Plans with chunks need a third internal
+ * vector in the workspace (midbf_workspace_size includes it).
+ * midbf_dplan_set_overlap: enable = 1 on (if the plan has chunks), 0 off.
+ * midbf_dplan_overlap: the chunk count in force (0: off).  EINVAL on null
+ * arguments. */
+int midbf_dplan_set_overlap(midbf_dplan* dp, int enable);
+int midbf_dplan_overlap(const midbf_dplan* dp, int* chunks);
+
 /* ---- CUDA graphs ----------------------------------------------------------
- * A sequence of midbf_apply / midbf_apply_batched / midbf_apply_noalloc
- * calls issued on one stream can be recorded once and replayed with one
+ * A sequence of midbf_apply / midbf_apply_batched calls issued on one
+ * stream can be recorded once and replayed with one
  * launch: midbf_capture_begin(stream), the apply calls on that stream, then
  * midbf_capture_end(stream, &graph); midbf_graph_launch(graph, s) replays
  * the whole sequence on any stream s of the same device, any number of
@@ -383,14 +459,22 @@ int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t*
  * calls no cudaMalloc, cudaFree or allocating library routine.
  *   - Arguments and layout are those of midbf_apply; dp's device must be the
  *     current device.
+ *   - The argument checks are those of midbf_apply (MIDBF_EINVAL for a null
+ *     pointer, nrhs <= 0, a short leading dimension, overlapping in/out,
+ *     vectors of 2^31 entries or more, or profiling on while the stream
+ *     records a graph).
  *   - Plans whose workspace for nrhs right-hand sides (midbf_workspace_size)
  *     exceeds the scratch size are rejected with MIDBF_EINVAL and a message
  *     saying how many bytes they need.
- *   - The first call on a device looks up the scratch array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The scratch array's device address is looked up (cudaGetSymbolAddress)
+ *     when the device plan is created, with its device current, and kept in
+ *     the plan; like the plan's other device memory it belongs to that
+ *     device's context and does not survive cudaDeviceReset.  If the lookup
+ *     failed, this call returns MIDBF_ECUDA with the reason.
  *   - All calls share the array and a call overwrites the previous call's
- *     contents; calls that overlap on the GPU (different streams, unordered
- *     host threads) race on it and give wrong results.
+ *     contents (nothing in it needs to start at zero); calls that overlap on
+ *     the GPU (different streams, unordered host threads) race on it and
+ *     give wrong results.
  * The paper has no counterpart to this call: it is an allocation policy of
  * this library, not a step of the method. */
 int midbf_apply_noalloc(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin,

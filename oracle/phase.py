@@ -15,7 +15,11 @@
 * LOWRANK: Psi(i, j) = sum_t U[i,t] V[j,t], the output form of Algorithm 7.
 
 Parity: pinned by closed forms in tests (DOT against the FFT, ZERO and
-SEPARABLE against rank one) and by hand-evaluated points.
+SEPARABLE against rank one) and by hand-evaluated points: FIO2D and
+FIO2D_JUMP in tests/golden/phase_values.txt, FIO3D in
+tests/golden/phase_values_3d.txt (points where every c_k is exact, chosen so
+that a wrong cyclic index or swapped sine and cosine change the value),
+DISTANCE against exact distances on the sphere mesh.
 """
 from __future__ import annotations
 

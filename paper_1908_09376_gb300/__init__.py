@@ -76,6 +76,17 @@ midbf_phase_lowrank = _sig("midbf_phase_lowrank", C.c_int,
 midbf_phase_recover = _sig("midbf_phase_recover", C.c_int,
                            [C.c_int, C.c_int64, _dblp, C.c_int64, _dblp, C.POINTER(midbf_access), C.c_int, C.c_int,
                             C.c_double, C.c_int, C.c_uint64, C.POINTER(_vp), C.POINTER(midbf_recover_info)])
+midbf_phase_recover_ex = _sig("midbf_phase_recover_ex", C.c_int,
+                              [C.c_int, C.c_int64, _dblp, C.c_int64, _dblp, C.POINTER(midbf_access), C.c_int,
+                               C.c_int, C.c_double, C.c_int, C.c_uint64, C.c_int, C.POINTER(_vp),
+                               C.POINTER(midbf_recover_info)])
+RECOVER_DEVICE = 1
+midbf_rpath_create = _sig("midbf_rpath_create", C.c_int, [C.c_int64, C.c_int64, _i64p, C.c_int64, C.POINTER(_vp)])
+midbf_rpath_destroy = _sig("midbf_rpath_destroy", None, [_vp])
+midbf_rpath_info = _sig("midbf_rpath_info", C.c_int, [_vp, _i64p, _i64p, C.POINTER(C.c_int)])
+midbf_recover_vectors = _sig("midbf_recover_vectors", C.c_int,
+                             [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_double, _vp, C.c_int64, _vp,
+                              C.c_int64, _vp, _vp])
 midbf_phase_eval = _sig("midbf_phase_eval", C.c_int, [_vp, C.c_int64, _i64p, _i64p, _dblp])
 midbf_phase_factors = _sig("midbf_phase_factors", C.c_int, [_vp, C.POINTER(C.c_int), _dblp, _dblp])
 midbf_phase_destroy = _sig("midbf_phase_destroy", None, [_vp])
@@ -98,6 +109,8 @@ midbf_apply = _sig("midbf_apply", C.c_int,
                    [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp, _vp, C.c_size_t])
 midbf_apply_host = _sig("midbf_apply_host", C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _vp, _vp, C.c_size_t])
 midbf_apply_launches = _sig("midbf_apply_launches", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)])
+midbf_dplan_set_overlap = _sig("midbf_dplan_set_overlap", C.c_int, [_vp, C.c_int])
+midbf_dplan_overlap = _sig("midbf_dplan_overlap", C.c_int, [_vp, C.POINTER(C.c_int)])
 midbf_dplan_status = _sig("midbf_dplan_status", C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)])
 midbf_dplan_profile = _sig("midbf_dplan_profile", C.c_int, [_vp, C.c_int])
 midbf_stage_times = _sig("midbf_stage_times", C.c_int,
@@ -177,8 +190,9 @@ class Phase:
         return Phase(h, X.shape[1], X.shape[0], W.shape[0])
 
     @staticmethod
-    def recover(X, W, rows_fn, cols_fn, r=4, q=2, tau=0.25, max_disc=16, seed=0):
-        """Algorithm 7 through the C ABI; rows_fn(idx) -> (len(idx), nw) complex K rows."""
+    def recover(X, W, rows_fn, cols_fn, r=4, q=2, tau=0.25, max_disc=16, seed=0, device=False):
+        """Algorithm 7 through the C ABI; rows_fn(idx) -> (len(idx), nw) complex K rows.
+        device=True runs every vector recovery (Algorithm 4) on the current CUDA device."""
         X, px = _f64(X)
         W, pw = _f64(W)
         nx, nw = X.shape[0], W.shape[0]
@@ -199,8 +213,9 @@ class Phase:
         acc = midbf_access(rcb, ccb, None)
         info = midbf_recover_info()
         h = _vp()
-        check(midbf_phase_recover(X.shape[1], nx, px, nw, pw, C.byref(acc), r, q, tau, max_disc, seed,
-                                  C.byref(h), C.byref(info)), "midbf_phase_recover")
+        check(midbf_phase_recover_ex(X.shape[1], nx, px, nw, pw, C.byref(acc), r, q, tau, max_disc, seed,
+                                     RECOVER_DEVICE if device else 0, C.byref(h), C.byref(info)),
+              "midbf_phase_recover_ex")
         ph = Phase(h, X.shape[1], nx, nw)
         ph.info = {f: getattr(info, f) for f, _ in midbf_recover_info._fields_}
         return ph
@@ -223,6 +238,51 @@ class Phase:
         check(midbf_phase_factors(self.h, C.byref(r), U.ctypes.data_as(_dblp), V.ctypes.data_as(_dblp)),
               "midbf_phase_factors")
         return U, V
+
+
+class RecoveryPath:
+    """A recovery path (Def. 3.3) on the current CUDA device for Algorithm 4:
+    edges is an (m, 2) integer array of (parent, child) pairs in path order."""
+
+    def __init__(self, n, edges, root=None):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int64).reshape(-1, 2))
+        if root is None:
+            root = int(e[0, 0]) if e.shape[0] else 0
+        self.n, self.nedges, self.root = int(n), int(e.shape[0]), int(root)
+        self.h = _vp()
+        check(midbf_rpath_create(self.n, self.nedges, e.ctypes.data_as(_i64p), self.root, C.byref(self.h)),
+              "midbf_rpath_create")
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            midbf_rpath_destroy(self.h)
+            self.h = _vp()
+
+    def runs(self):
+        nr = C.c_int()
+        check(midbf_rpath_info(self.h, None, None, C.byref(nr)), "midbf_rpath_info")
+        return nr.value
+
+    def recover(self, u, tau, v0=None, stream=None):
+        """Algorithm 4 for the rows of u (a (nvec, n) float64 CUDA tensor of
+        observations modulo one), starting from v0 (default: u).  Returns
+        (v, flags, D): recovered values, per-edge flags (uint8) and, per
+        vector, the list D of the root and the flagged children."""
+        import torch
+        u = u.contiguous()
+        nvec = u.shape[0]
+        v = (u if v0 is None else v0).clone().contiguous()
+        flags = torch.zeros((nvec, max(1, self.nedges)), dtype=torch.uint8, device=u.device)
+        D = torch.zeros((nvec, self.nedges + 1), dtype=torch.int64, device=u.device)
+        nD = torch.zeros(nvec, dtype=torch.int64, device=u.device)
+        s = torch.cuda.current_stream(u.device) if stream is None else stream
+        check(midbf_recover_vectors(self.h, nvec, u.data_ptr(), self.n, v.data_ptr(), self.n, float(tau),
+                                    flags.data_ptr(), flags.shape[1], D.data_ptr(), D.shape[1], nD.data_ptr(),
+                                    s.cuda_stream), "midbf_recover_vectors")
+        s.synchronize()
+        nd = nD.cpu().numpy()
+        Dh = D.cpu().numpy()
+        return v, flags[:, :self.nedges], [Dh[k, :nd[k]].tolist() for k in range(nvec)]
 
 
 def params(d, **kw):
@@ -340,6 +400,15 @@ class DevicePlan:
         n = C.c_int()
         check(midbf_apply_launches(self.h, nrhs, C.byref(n)), "midbf_apply_launches")
         return n.value
+
+    def set_overlap(self, enable=True):
+        """Overlap the middle factor with its neighbouring U stage (chunked, on a side stream)."""
+        check(midbf_dplan_set_overlap(self.h, int(enable)), "midbf_dplan_set_overlap")
+
+    def overlap(self):
+        v = C.c_int()
+        check(midbf_dplan_overlap(self.h, C.byref(v)), "midbf_dplan_overlap")
+        return v.value
 
     def profile(self, enable=True):
         check(midbf_dplan_profile(self.h, int(enable)), "midbf_dplan_profile")

@@ -92,17 +92,27 @@ int midbf_phase_lowrank(int d, int64_t nx, const double* X, int64_t nw, const do
     });
 }
 
-int midbf_phase_recover(int d, int64_t nx, const double* X, int64_t nw, const double* W, const midbf_access* acc,
-                        int r, int q, double tau, int max_disc, uint64_t seed, midbf_phase** out,
-                        midbf_recover_info* info) {
+int midbf_phase_recover_ex(int d, int64_t nx, const double* X, int64_t nw, const double* W,
+                           const midbf_access* acc, int r, int q, double tau, int max_disc, uint64_t seed,
+                           int flags, midbf_phase** out, midbf_recover_info* info) {
     return guarded([&] {
         if (!out || !acc || !acc->rows_fn || !acc->cols_fn) fail(MIDBF_EINVAL, "null argument");
+        if (flags & ~MIDBF_RECOVER_DEVICE) fail(MIDBF_EINVAL, "unknown flags");
         check_points(d, nx, X, nw, W);
         if (r <= 0 || q <= 0 || (int64_t)r * q > std::min(nx, nw)) fail(MIDBF_EINVAL, "bad rank / oversampling");
         if (!(tau > 0.0 && tau <= 0.5)) fail(MIDBF_EINVAL, "tau must be in (0, 1/2]");
-        auto ph = recover_phase(d, nx, X, nw, W, *acc, r, q, tau, max_disc, seed, info);
+        if ((flags & MIDBF_RECOVER_DEVICE) && (nx >= (int64_t(1) << 31) || nw >= (int64_t(1) << 31)))
+            fail(MIDBF_EINVAL, "device recovery needs fewer than 2^31 points");
+        auto ph = recover_phase(d, nx, X, nw, W, *acc, r, q, tau, max_disc, seed, info,
+                                (flags & MIDBF_RECOVER_DEVICE) != 0);
         *out = reinterpret_cast<midbf_phase*>(ph.release());
     });
+}
+
+int midbf_phase_recover(int d, int64_t nx, const double* X, int64_t nw, const double* W, const midbf_access* acc,
+                        int r, int q, double tau, int max_disc, uint64_t seed, midbf_phase** out,
+                        midbf_recover_info* info) {
+    return midbf_phase_recover_ex(d, nx, X, nw, W, acc, r, q, tau, max_disc, seed, 0, out, info);
 }
 
 int midbf_phase_eval(const midbf_phase* ph, int64_t n, const int64_t* ix, const int64_t* iw, double* out) {

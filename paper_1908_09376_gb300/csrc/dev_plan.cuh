@@ -42,10 +42,24 @@ struct DevBuf {
     size_t n = 0;
 };
 
+// The middle factor and the interpolation stage next to it (forward: S then
+// the first U stage; adjoint: that U stage's adjoint then S's) can overlap:
+// their blocks fall into groups such that each U block reads only outputs of
+// S blocks in its own group, so the two stages run chunk by chunk, chunk k of
+// the second stage on a side stream after chunk k of the first.  Work items
+// of the two stages are stored grouped by chunk, and ck_* hold the item
+// offsets of every chunk (kMaxChunks at most).
+constexpr int kMaxChunks = 8;
+constexpr int kDefaultChunks = 4;   // chunks prepared at creation and used by default
+
 struct DevStageBase {
     int kind = KIND_V;
     int64_t in_len = 0, out_len = 0;
     bool out_user = false, in_user = false;
+    int nchunks = 0;   // 0: the stage is not split
+    int ck_r[kMaxChunks + 1] = {}, ck_c[kMaxChunks + 1] = {}, ck_c1[kMaxChunks + 1] = {};
+    int ck_rows[kMaxChunks + 1] = {}, ck_rows4[kMaxChunks + 1] = {}, ck_cols[kMaxChunks + 1] = {},
+        ck_cols4[kMaxChunks + 1] = {};
 };
 
 template <class R>
@@ -64,6 +78,7 @@ struct DevStage : DevStageBase {
     const int2* items_rows4 = nullptr;  // 128-row items (RT = 4)
     const int2* items_cols4 = nullptr;
     int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
+    int n4_rows_stage = 0, n4_cols_stage = 0;   // 128-row items of the whole stage (item-size rule)
     bool s_dist = false;                // square-root term in the distance form (DISTANCE phase)
     // tensor-core modes: dense BF16 tile images of the V/U blocks,
     // [0] forward orientation (stage input -> output), [1] adjoint
@@ -93,6 +108,20 @@ struct midbf_dplan {
     int* d_status = nullptr;      // device status word written by bounded waits
     int s_mode = MIDBF_S_ONTHEFLY;
     int device = 0;
+    void* noalloc_scratch = nullptr;   // device address of midbf_apply_noalloc's scratch array
+    std::string noalloc_err;           // why the lookup failed, when it did
+    // overlap of the middle factor with its neighbouring U stage (see DevStageBase):
+    // s_stage = index of the middle factor (-1: none); chunks_built = chunks prepared
+    // at creation (0: none); chunks = chunks_built while the overlap is on, else 0.
+    // Plans with chunks give the U stage's internal output space a third workspace
+    // vector, since the stage before the middle factor reads the ping-pong buffer it
+    // would otherwise write.
+    int s_stage = -1;
+    int chunks = 0;
+    int chunks_built = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_ck[midbf_gpu::kMaxChunks] = {};
+    mutable std::mutex pipe_mu;        // one overlapped apply of this plan issued at a time
     int64_t nx = 0, nw = 0;
     int64_t max_space = 0;        // longest internal vector space
     size_t factor_bytes = 0, index_bytes = 0;
@@ -119,6 +148,11 @@ struct midbf_dplan {
     mutable int last_nrhs = 1;
     ~midbf_dplan() {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : ev_ck)
+            if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
         if (d_status) cudaFree(d_status);
         for (void* p : allocs) cudaFree(p);
     }
@@ -177,10 +211,14 @@ inline bool valid_choice(int choice) {
            base == 8 || base == 16;
 }
 
-// Bytes of the two ping-pong vectors of the workspace, rounded up to 256.
+// Internal vectors of the workspace: the two ping-pong vectors, and a third
+// one when the middle factor overlaps its U stage.
+inline int vec_buffers(const midbf_dplan* dp) { return dp->chunks_built > 1 ? 3 : 2; }
+
+// Bytes of the workspace's internal vectors, rounded up to 256.
 inline size_t vec_workspace_bytes(const midbf_dplan* dp, int nrhs) {
     const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-    const size_t b = 2 * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
+    const size_t b = (size_t)vec_buffers(dp) * (size_t)std::max<int64_t>(dp->max_space, 1) * (size_t)nrhs * ce;
     return (b + 255) / 256 * 256;
 }
 

@@ -151,10 +151,84 @@ void make_tc_images(midbf_dplan* dp, const Stage& st, DevStage<R>& ds) {
     ds.tc = true;
 }
 
+// Chunks for the overlap of the middle factor (stage si) with the first U
+// stage (si + 1): the blocks of S that a U block reads are joined into one
+// group (union-find over the U blocks' inputs, found through the positions S
+// writes), then whole groups are dealt to at most nch chunks of about equal
+// work (entries of S and of the U stage's T), in block order.  Every U block
+// reads only S blocks of its own chunk.  Returns false when there are fewer
+// than two groups.
+bool overlap_chunks(const Plan& pl, int si, int nch, std::vector<int>& ck_s, std::vector<int>& ck_u) {
+    if (si < 0 || si + 1 >= (int)pl.stages.size() || pl.stages[si + 1].kind != KIND_U || nch < 2) return false;
+    const Stage& S = pl.stages[si];
+    const Stage& U = pl.stages[si + 1];
+    const int ns = (int)S.blocks.size(), nu = (int)U.blocks.size();
+    std::vector<int> owner((size_t)S.out_len, -1), parent(ns);
+    std::iota(parent.begin(), parent.end(), 0);
+    std::function<int(int)> find = [&](int a) {
+        while (parent[a] != a) a = parent[a] = parent[parent[a]];
+        return a;
+    };
+    for (int b = 0; b < ns; ++b)
+        for (int64_t p : S.blocks[b].out_idx) owner[p] = b;
+    std::vector<int> first(nu, -1);
+    for (int b = 0; b < nu; ++b)
+        for (int64_t p : U.blocks[b].in_idx) {
+            const int o = owner[p];
+            if (o < 0) fail(MIDBF_EINTERNAL, "U stage reads a position the middle factor does not write");
+            if (first[b] < 0) first[b] = o;
+            else parent[find(o)] = find(first[b]);
+        }
+    // group weights and group order (by smallest S block)
+    std::vector<int> gid(ns, -1);
+    std::vector<double> gw;
+    for (int b = 0; b < ns; ++b) {
+        const int r = find(b);
+        if (gid[r] < 0) {
+            gid[r] = (int)gw.size();
+            gw.push_back(0.0);
+        }
+        gid[b] = gid[r];
+        gw[gid[b]] += (double)S.blocks[b].out_idx.size() * (double)S.blocks[b].in_idx.size();
+    }
+    for (int b = 0; b < nu; ++b) {
+        if (first[b] < 0) continue;
+        for (const Sub& sb : U.blocks[b].subs) gw[gid[first[b]]] += (double)sb.k * (double)(sb.m - sb.k);
+    }
+    const int ng = (int)gw.size();
+    if (ng < 2) return false;
+    nch = std::min(nch, ng);
+    const double total = std::accumulate(gw.begin(), gw.end(), 0.0);
+    std::vector<int> gchunk(ng);
+    double acc = 0.0;
+    for (int g = 0; g < ng; ++g) {
+        gchunk[g] = std::min(nch - 1, (int)(acc / total * nch));
+        acc += gw[g];
+    }
+    ck_s.assign(ns, 0);
+    ck_u.assign(nu, 0);
+    for (int b = 0; b < ns; ++b) ck_s[b] = gchunk[gid[b]];
+    for (int b = 0; b < nu; ++b) ck_u[b] = first[b] < 0 ? 0 : gchunk[gid[first[b]]];
+    return true;
+}
+
+// Stable reorder of a work-item list by the chunk of each item's block, and
+// the item offset of every chunk (off has nch + 1 entries).
+template <class It, class BlockOf>
+void group_items(std::vector<It>& items, const std::vector<int>& chunk_of_block, int nch, BlockOf block_of, int* off) {
+    std::stable_sort(items.begin(), items.end(), [&](const It& a, const It& b) {
+        return chunk_of_block[block_of(a)] < chunk_of_block[block_of(b)];
+    });
+    for (int k = 0; k <= nch; ++k) off[k] = 0;
+    for (const It& it : items) off[chunk_of_block[block_of(it)] + 1]++;
+    for (int k = 0; k < nch; ++k) off[k + 1] += off[k];
+}
+
 // Build the device arrays of an ID stage (V or U), or of a stored S stage
 // seen as dense blocks with no skeleton.
 template <class R>
-void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds, bool stored_s) {
+void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds, bool stored_s,
+                   const std::vector<int>* chunk_of_block = nullptr, int nch = 0) {
     std::vector<SubDesc> subs;
     std::vector<BlockDesc> blocks;
     std::vector<int> skel, red, wide_pos, narrow_pos;
@@ -280,6 +354,12 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     const int rt = rows_per_lane(maxk);
     for (size_t s = 0; s < subs.size(); ++s)
         for (int r0 = 0; r0 < subs[s].k; r0 += 32 * rt) items_r.push_back({(int)s, r0});
+    if (chunk_of_block && nch > 1) {
+        group_items(items_r, *chunk_of_block, nch, [&](const ItemR& it) { return subs[it.sub].block; }, ds.ck_r);
+        group_items(items_c, *chunk_of_block, nch, [](const ItemC& it) { return it.block; }, ds.ck_c);
+        group_items(items_c1, *chunk_of_block, nch, [](const ItemC& it) { return it.block; }, ds.ck_c1);
+        ds.nchunks = nch;
+    }
     ds.id = true;
     ds.rt = rt;
     ds.n_items_r = (int)items_r.size();
@@ -425,7 +505,8 @@ void phase_split(const Phase& ph, const Block& bk, int P, int Q, SplitOut& rows,
 }
 
 template <class R>
-void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds) {
+void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>& ds,
+                  const std::vector<int>* chunk_of_block = nullptr, int nch = 0) {
     const Phase& ph = pl.phase;
     int P = 0, Q = 0;
     switch (ph.family) {
@@ -468,6 +549,14 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
         for (int r0 = 0; r0 < blk_nrow[b]; r0 += 128) it_rows4.push_back(make_int2((int)b, r0));
         for (int c0 = 0; c0 < blk_ncol[b]; c0 += 128) it_cols4.push_back(make_int2((int)b, c0));
     }
+    if (chunk_of_block && nch > 1) {
+        auto blk = [](const int2& it) { return it.x; };
+        group_items(it_rows, *chunk_of_block, nch, blk, ds.ck_rows);
+        group_items(it_cols, *chunk_of_block, nch, blk, ds.ck_cols);
+        group_items(it_rows4, *chunk_of_block, nch, blk, ds.ck_rows4);
+        group_items(it_cols4, *chunk_of_block, nch, blk, ds.ck_cols4);
+        ds.nchunks = nch;
+    }
     ds.ss.P = P;
     ds.ss.Q = Q;
     ds.ss.blk_rows = upload(dp, blk_rows, &dp->index_bytes);
@@ -490,6 +579,8 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     ds.n_items_cols = (int)it_cols.size();
     ds.n_items_rows4 = (int)it_rows4.size();
     ds.n_items_cols4 = (int)it_cols4.size();
+    ds.n4_rows_stage = ds.n_items_rows4;
+    ds.n4_cols_stage = ds.n_items_cols4;
     if constexpr (sizeof(R) == 4) {
         if (dp->tc_mode) {
             // B-image chunks of the middle factor's input: forward the columns
@@ -519,8 +610,20 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
 template <class R>
 void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out, Plan* consume) {
     int64_t in_len = pl.phase.nw;
+    // overlap groups of the middle factor and the U stage after it
+    std::vector<int> ck_s, ck_u;
+    int si = -1;
+    for (size_t s = 0; s < pl.stages.size(); ++s)
+        if (pl.stages[s].kind == KIND_S) si = (int)s;
+    dp->s_stage = si;
+    const bool grouped = overlap_chunks(pl, si, kDefaultChunks, ck_s, ck_u);
+    int nch = 0;
+    if (grouped) nch = 1 + std::max(*std::max_element(ck_s.begin(), ck_s.end()), *std::max_element(ck_u.begin(), ck_u.end()));
+    dp->chunks_built = grouped ? nch : 0;
+    dp->chunks = dp->chunks_built;
     for (size_t s = 0; s < pl.stages.size(); ++s) {
         const Stage& st = pl.stages[s];
+        const std::vector<int>* ck = !grouped ? nullptr : (int)s == si ? &ck_s : (int)s == si + 1 ? &ck_u : nullptr;
         DevStage<R> ds;
         ds.kind = st.kind;
         ds.in_len = in_len;
@@ -529,10 +632,10 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out,
         ds.out_user = st.out_user != 0;
         const size_t f0 = dp->factor_bytes, i0 = dp->index_bytes;
         if (st.kind == KIND_S) {
-            if (dp->s_mode == MIDBF_S_STORED) make_id_stage<R>(dp, pl, st, ds, true);
-            else make_s_stage<R>(dp, pl, st, ds);
+            if (dp->s_mode == MIDBF_S_STORED) make_id_stage<R>(dp, pl, st, ds, true, ck, nch);
+            else make_s_stage<R>(dp, pl, st, ds, ck, nch);
         } else {
-            make_id_stage<R>(dp, pl, st, ds, false);
+            make_id_stage<R>(dp, pl, st, ds, false, ck, nch);
             if (consume) {
                 for (Block& bk : consume->stages[s].blocks)
                     for (Sub& sb : bk.subs) {
@@ -656,16 +759,76 @@ void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, Ve
     }
 }
 
+// The work items of chunk k of a split stage: a shallow copy whose item lists
+// and counts cover that chunk only.
+template <class R>
+DevStage<R> chunk_view(const DevStage<R>& ds, int k) {
+    DevStage<R> v = ds;
+    auto cut = [k](auto& ptr, int& n, const int* off) {
+        if (ptr) ptr += off[k];
+        n = off[k + 1] - off[k];
+    };
+    if (ds.id) {
+        cut(v.ids.items_r, v.n_items_r, ds.ck_r);
+        cut(v.ids.items_c, v.n_items_c, ds.ck_c);
+        cut(v.ids1.items_c, v.n_items_c1, ds.ck_c1);
+    } else {
+        cut(v.items_rows, v.n_items_rows, ds.ck_rows);
+        cut(v.items_rows4, v.n_items_rows4, ds.ck_rows4);
+        cut(v.items_cols, v.n_items_cols, ds.ck_cols);
+        cut(v.items_cols4, v.n_items_cols4, ds.ck_cols4);
+    }
+    return v;
+}
+
+// Whether a stage launch runs on the tensor cores (mirrors launch_stage).
+template <class R>
+bool stage_uses_tc(const midbf_dplan* dp, const DevStage<R>& ds, int nrhs, int choice) {
+    if (sizeof(R) != 4) return false;
+    const bool tc_ok = ds.id ? ds.tc : dp->tc_mode != 0;
+    return tc_ok && (choice == MIDBF_CHOICE_TENSOR ||
+                     (choice == MIDBF_CHOICE_DEFAULT && nrhs >= (ds.id ? kTcBlkMinRhs : kTcMinRhs)));
+}
+
+// Whether an apply overlaps the middle factor with its U stage: chunks on,
+// profiling off (per-stage events need the stages one after the other), and
+// both stages on the SIMT kernels.
+template <class R>
+bool overlapped(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, int nrhs, bool adjoint) {
+    const int si = dp->s_stage;
+    if (dp->chunks < 2 || dp->profile || si < 0 || si + 1 >= (int)stages.size()) return false;
+    if (stages[si].nchunks != dp->chunks_built || stages[si + 1].nchunks != dp->chunks_built) return false;
+    return !stage_uses_tc(dp, stages[si], nrhs, tuned_choice(dp, nrhs, si, adjoint)) &&
+           !stage_uses_tc(dp, stages[si + 1], nrhs, tuned_choice(dp, nrhs, si + 1, adjoint));
+}
+
 // Run all stages.  user_in/user_out: caller vectors (column-major with ld).
+//
+// With the overlap on, the middle factor S (stage si) and the U stage after
+// it run as chunks: forward, chunk k of S on the caller's stream, then chunk
+// k of U on the plan's side stream after an event; adjoint, chunk k of U's
+// adjoint first, then chunk k of S's adjoint on the side stream.  The side
+// stream forks from the caller's stream before the pair and joins it after,
+// so the apply stays ordered on the caller's stream (and records into a
+// graph as one fork and join).  U's internal output space lives in the third
+// workspace vector: with two, it would share a buffer with the input of S,
+// which later chunks of S still read.
 template <class R>
 void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adjoint, const void* in, int64_t ldin,
          void* out, int64_t ldout, int nrhs, cudaStream_t s, void* ws) {
     const int ns = (int)stages.size();
-    cx<R>* buf[2] = {static_cast<cx<R>*>(ws), static_cast<cx<R>*>(ws) + dp->max_space * nrhs};
+    cx<R>* buf[3] = {static_cast<cx<R>*>(ws), static_cast<cx<R>*>(ws) + dp->max_space * nrhs,
+                     static_cast<cx<R>*>(ws) + 2 * dp->max_space * nrhs};
     __nv_bfloat16* bimg = reinterpret_cast<__nv_bfloat16*>(static_cast<char*>(ws) + vec_workspace_bytes(dp, nrhs));
     VecRef<R> uin{(cx<R>*)in, 1, ldin};
     VecRef<R> uout{(cx<R>*)out, 1, ldout};
-    auto internal = [&](int space) { return VecRef<R>{buf[space & 1], nrhs, 1}; };
+    const bool third = vec_buffers(dp) == 3;
+    auto internal = [&](int space) {
+        return VecRef<R>{third && space == dp->s_stage + 1 ? buf[2] : buf[space & 1], nrhs, 1};
+    };
+    const bool pipe = overlapped(dp, stages, nrhs, adjoint);
+    std::unique_lock<std::mutex> lk(dp->pipe_mu, std::defer_lock);
+    if (pipe) lk.lock();
     if (dp->profile) {
         while ((int)dp->ev.size() < 2 * ns) {
             cudaEvent_t e;
@@ -675,18 +838,41 @@ void run(const midbf_dplan* dp, const std::vector<DevStage<R>>& stages, bool adj
         dp->ev_stage.assign(ns, 0);
         dp->last_nrhs = nrhs;
     }
+    // forward: stage sidx reads space sidx-1 (user in for 0) and writes space sidx.
+    auto io = [&](int sidx, VecRef<R>& src, VecRef<R>& dst) {
+        VecRef<R> fin = sidx == 0 ? (adjoint ? uout : uin) : internal(sidx - 1);
+        VecRef<R> fout = stages[sidx].out_user ? (adjoint ? uin : uout) : internal(sidx);
+        src = adjoint ? fout : fin;
+        dst = adjoint ? fin : fout;
+    };
     for (int q = 0; q < ns; ++q) {
         const int sidx = adjoint ? ns - 1 - q : q;
         const DevStage<R>& ds = stages[sidx];
+        VecRef<R> src, dst;
+        io(sidx, src, dst);
+        if (pipe && sidx == (adjoint ? dp->s_stage + 1 : dp->s_stage)) {
+            // the overlapped pair: this stage (first) and the next one in launch order (second)
+            const int sidx2 = adjoint ? dp->s_stage : dp->s_stage + 1;
+            VecRef<R> src2, dst2;
+            io(sidx2, src2, dst2);
+            const int c1 = tuned_choice(dp, nrhs, sidx, adjoint), c2 = tuned_choice(dp, nrhs, sidx2, adjoint);
+            CK(cudaEventRecord(dp->ev_fork, s));
+            CK(cudaStreamWaitEvent(dp->side, dp->ev_fork, 0));
+            for (int k = 0; k < dp->chunks; ++k) {
+                launch_stage<R>(dp, chunk_view(ds, k), adjoint, src, dst, nrhs, c1, bimg, s);
+                CK(cudaEventRecord(dp->ev_ck[k], s));
+                CK(cudaStreamWaitEvent(dp->side, dp->ev_ck[k], 0));
+                launch_stage<R>(dp, chunk_view(stages[sidx2], k), adjoint, src2, dst2, nrhs, c2, bimg, dp->side);
+            }
+            CK(cudaEventRecord(dp->ev_join, dp->side));
+            CK(cudaStreamWaitEvent(s, dp->ev_join, 0));
+            ++q;
+            continue;
+        }
         if (dp->profile) {
             dp->ev_stage[q] = sidx;
             CK(cudaEventRecord(dp->ev[2 * q], s));
         }
-        // forward: stage sidx reads space sidx-1 (user in for 0) and writes space sidx.
-        VecRef<R> fin = sidx == 0 ? (adjoint ? uout : uin) : internal(sidx - 1);
-        VecRef<R> fout = ds.out_user ? (adjoint ? uin : uout) : internal(sidx);
-        VecRef<R> src = adjoint ? fout : fin;
-        VecRef<R> dst = adjoint ? fin : fout;
         launch_stage<R>(dp, ds, adjoint, src, dst, nrhs, tuned_choice(dp, nrhs, sidx, adjoint), bimg, s);
         if (dp->profile) CK(cudaEventRecord(dp->ev[2 * q + 1], s));
     }
@@ -799,6 +985,28 @@ bool capturing(cudaStream_t s) {
     CK(cudaStreamIsCapturing(s, &st));
     return st != cudaStreamCaptureStatusNone;
 }
+
+// Checks shared by the apply entry points (midbf_apply, midbf_apply_noalloc):
+// handles and pointers, RHS count, leading dimensions, disjoint in/out, the
+// 32-bit position maps, and no profiling events inside a graph recording.
+void check_apply_args(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, const void* out,
+                      int64_t ldout, int nrhs, cudaStream_t s) {
+    if (!dp || !in || !out) fail(MIDBF_EINVAL, "null argument");
+    if (nrhs <= 0) fail(MIDBF_EINVAL, "nrhs must be positive");
+    const int64_t nin = adjoint ? dp->nx : dp->nw;
+    const int64_t nout = adjoint ? dp->nw : dp->nx;
+    if (ldin < nin || ldout < nout) fail(MIDBF_EINVAL, "leading dimension smaller than the vector length");
+    const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
+    const char* ib = static_cast<const char*>(in);
+    const char* ob = static_cast<const char*>(out);
+    const size_t inb = ((size_t)(nrhs - 1) * ldin + nin) * ce, outb = ((size_t)(nrhs - 1) * ldout + nout) * ce;
+    if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
+    if (dp->nw >= (1LL << 31) || dp->nx >= (1LL << 31)) fail(MIDBF_EINVAL, "vectors longer than 2^31");
+    if (dp->profile && capturing(s)) fail(MIDBF_EINVAL, "profiling is on: the apply cannot be recorded into a graph");
+}
+
+// Scratch array of midbf_apply_noalloc (defined at the end of this file).
+void* noalloc_lookup(std::string& err);
 
 }  // namespace
 
@@ -927,6 +1135,7 @@ int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags
         if (dp->tc_mode && s_mode != MIDBF_S_ONTHEFLY) fail(MIDBF_EINVAL, "the tensor-core modes generate the middle factor on the fly");
         dp->s_mode = s_mode;
         CK(cudaGetDevice(&dp->device));
+        dp->noalloc_scratch = noalloc_lookup(dp->noalloc_err);   // for midbf_apply_noalloc
         dp->nx = pl.nx();
         dp->nw = pl.nw();
         if (cudaMalloc(&dp->d_status, sizeof(int)) != cudaSuccess) fail(MIDBF_ENOMEM, "cudaMalloc of the status word failed");
@@ -934,6 +1143,13 @@ int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags
         if (consume) plw.released = true;   // from here on, whatever happens below
         if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32, consume);
         else make_stages<double>(dp.get(), pl, dp->st64, consume);
+        if (dp->chunks_built > 1) {
+            // the side stream and events of the overlap (no device memory)
+            CK(cudaStreamCreateWithFlags(&dp->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&dp->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&dp->ev_join, cudaEventDisableTiming));
+            for (int k = 0; k < dp->chunks_built; ++k) CK(cudaEventCreateWithFlags(&dp->ev_ck[k], cudaEventDisableTiming));
+        }
         CK(cudaDeviceSynchronize());
         *out = dp.release();
         return MIDBF_OK;
@@ -1021,7 +1237,29 @@ int midbf_apply_launches(const midbf_dplan* dp, int nrhs, int* launches) {
     };
     if (dp->precision == MIDBF_FP32) count(dp->st32);
     else count(dp->st64);
+    // the overlapped pair runs each of its two stages as one launch per chunk
+    const bool pipe = dp->precision == MIDBF_FP32 ? overlapped(dp, dp->st32, nrhs, false)
+                                                  : overlapped(dp, dp->st64, nrhs, false);
+    if (pipe) n += 2 * (dp->chunks - 1);
     *launches = n;
+    return MIDBF_OK;
+}
+
+int midbf_dplan_set_overlap(midbf_dplan* dp, int enable) {
+    if (!dp) {
+        set_last_error("midbf_dplan_set_overlap: null plan");
+        return MIDBF_EINVAL;
+    }
+    dp->chunks = enable ? dp->chunks_built : 0;
+    return MIDBF_OK;
+}
+
+int midbf_dplan_overlap(const midbf_dplan* dp, int* chunks) {
+    if (!dp || !chunks) {
+        set_last_error("midbf_dplan_overlap: null argument");
+        return MIDBF_EINVAL;
+    }
+    *chunks = dp->chunks;
     return MIDBF_OK;
 }
 
@@ -1075,22 +1313,11 @@ int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t*
 int midbf_apply(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, void* out, int64_t ldout,
                 int nrhs, void* stream, void* workspace, size_t workspace_bytes) {
     try {
-        if (!dp || !in || !out) fail(MIDBF_EINVAL, "null argument");
-        if (nrhs <= 0) fail(MIDBF_EINVAL, "nrhs must be positive");
-        const int64_t nin = adjoint ? dp->nx : dp->nw;
-        const int64_t nout = adjoint ? dp->nw : dp->nx;
-        if (ldin < nin || ldout < nout) fail(MIDBF_EINVAL, "leading dimension smaller than the vector length");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        check_apply_args(dp, adjoint, in, ldin, out, ldout, nrhs, s);
         size_t need = 0;
         midbf_workspace_size(dp, nrhs, &need);
         if (!workspace || workspace_bytes < need) fail(MIDBF_EINVAL, "workspace too small: need " + std::to_string(need) + " bytes");
-        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-        const char* ib = static_cast<const char*>(in);
-        const char* ob = static_cast<const char*>(out);
-        const size_t inb = ((size_t)(nrhs - 1) * ldin + nin) * ce, outb = ((size_t)(nrhs - 1) * ldout + nout) * ce;
-        if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
-        if (dp->nw >= (1LL << 31) || dp->nx >= (1LL << 31)) fail(MIDBF_EINVAL, "vectors longer than 2^31");
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        if (dp->profile && capturing(s)) fail(MIDBF_EINVAL, "profiling is on: the apply cannot be recorded into a graph");
         if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
         else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, workspace);
         return MIDBF_OK;
@@ -1227,26 +1454,23 @@ constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
 }
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-namespace {
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[256] = {};  // device address of the scratch array, per device
-
-// Device address of the scratch array on the current device.  The host-side
-// name g_noalloc_scratch is only a stand-in, never a device address, so the
-// address is looked up once per device with that device current.
-void* noalloc_scratch(int dev) {
-    if (dev < 0 || dev >= 256) fail(MIDBF_EINVAL, "device ordinal out of range");
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            fail(MIDBF_ECUDA, std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e));
-        g_noalloc_ptr[dev] = ptr;
+namespace midbf_gpu {
+// Device address of the scratch array in the current device's context.  The
+// host-side name g_noalloc_scratch is only a stand-in, never a device address,
+// so midbf_dplan_create_ex looks the address up with the plan's device
+// current and keeps it in the plan: a plan, like its device memory, lives in
+// one context, and the lookup (which may load the module) happens at set-up,
+// before any stream capture.
+void* noalloc_lookup(std::string& err) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+        err = std::string("cudaGetSymbolAddress of the scratch array failed: ") + cudaGetErrorString(e);
+        return nullptr;
     }
-    return g_noalloc_ptr[dev];
+    return ptr;
 }
-}  // namespace
+}  // namespace midbf_gpu
 
 extern "C" {
 
@@ -1255,11 +1479,8 @@ size_t midbf_noalloc_scratch_bytes(void) { return kNoAllocScratchBytes; }
 int midbf_apply_noalloc(const midbf_dplan* dp, int adjoint, const void* in, int64_t ldin, void* out, int64_t ldout,
                         int nrhs, void* stream) {
     try {
-        if (!dp || !in || !out) fail(MIDBF_EINVAL, "null argument");
-        if (nrhs <= 0) fail(MIDBF_EINVAL, "nrhs must be positive");
-        const int64_t nin = adjoint ? dp->nx : dp->nw;
-        const int64_t nout = adjoint ? dp->nw : dp->nx;
-        if (ldin < nin || ldout < nout) fail(MIDBF_EINVAL, "leading dimension smaller than the vector length");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        check_apply_args(dp, adjoint, in, ldin, out, ldout, nrhs, s);
         size_t need = 0;
         midbf_workspace_size(dp, nrhs, &need);
         if (need > kNoAllocScratchBytes)
@@ -1268,18 +1489,13 @@ int midbf_apply_noalloc(const midbf_dplan* dp, int adjoint, const void* in, int6
                                    " right-hand sides, more than the built-in " +
                                    std::to_string(kNoAllocScratchBytes) +
                                    " bytes; use midbf_apply with a caller workspace or fewer right-hand sides");
-        const size_t ce = dp->precision == MIDBF_FP32 ? 8 : 16;
-        const char* ib = static_cast<const char*>(in);
-        const char* ob = static_cast<const char*>(out);
-        const size_t inb = ((size_t)(nrhs - 1) * ldin + nin) * ce, outb = ((size_t)(nrhs - 1) * ldout + nout) * ce;
-        if (ib < ob + outb && ob < ib + inb) fail(MIDBF_EINVAL, "input and output overlap");
         int dev = 0;
         CK(cudaGetDevice(&dev));
         if (dev != dp->device) fail(MIDBF_EINVAL, "the current device is not the device of this plan");
-        void* scratch = noalloc_scratch(dev);
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        if (dp->precision == MIDBF_FP32) run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, scratch);
-        else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, scratch);
+        if (!dp->noalloc_scratch) fail(MIDBF_ECUDA, dp->noalloc_err);
+        if (dp->precision == MIDBF_FP32)
+            run<float>(dp, dp->st32, adjoint != 0, in, ldin, out, ldout, nrhs, s, dp->noalloc_scratch);
+        else run<double>(dp, dp->st64, adjoint != 0, in, ldin, out, ldout, nrhs, s, dp->noalloc_scratch);
         return MIDBF_OK;
     } catch (const Error& e) {
         set_last_error(e.what());

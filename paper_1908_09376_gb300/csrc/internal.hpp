@@ -131,9 +131,21 @@ void phase_check(const Phase& ph);
 std::unique_ptr<Plan> build_plan(const Phase& ph, const midbf_params& prm);
 
 // recover.cpp
+// device = true: every vector recovery of Algorithm 4 (the detection along the
+// root row and column, and each piece of Algorithm 6) runs on the current CUDA
+// device (recover_gpu.cu); the results are the same bit for bit.
 std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t nw, const double* W,
                                      const midbf_access& acc, int r, int q, double tau, int max_disc,
-                                     uint64_t seed, midbf_recover_info* info);
+                                     uint64_t seed, midbf_recover_info* info, bool device = false);
+
+// recover_gpu.cu: Algorithm 4 on the device.  device_recover_along recovers the
+// host vectors vs[k] (start values in place) from the observations us[k]
+// along the edges E of a path piece rooted at root; device_detect returns D
+// (the path root, then the flagged children in path order) for u along P.
+void device_recover_along(int64_t n, const std::vector<std::pair<int64_t, int64_t>>& E, int64_t root,
+                          const std::vector<const double*>& us, const std::vector<double*>& vs);
+std::vector<int64_t> device_detect(const std::vector<double>& u, const std::vector<std::pair<int64_t, int64_t>>& P,
+                                   double tau);
 
 // qr.cpp: column interpolative decomposition of a dense column-major matrix
 struct IdResult {

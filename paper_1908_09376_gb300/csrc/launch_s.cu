@@ -10,6 +10,7 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
     const bool four = RT == 4;
     st.items = !CJ ? (four ? ds.items_rows4 : ds.items_rows) : (four ? ds.items_cols4 : ds.items_cols);
     const int n = !CJ ? (four ? ds.n_items_rows4 : ds.n_items_rows) : (four ? ds.n_items_cols4 : ds.n_items_cols);
+    if (n == 0) return;
     const SSide<R>& rside = !CJ ? ds.srows : ds.scols;
     const SSide<R>& cside = !CJ ? ds.scols : ds.srows;
     if (persist) {
@@ -32,7 +33,7 @@ void launch_s_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
 template <class R, bool CJ, int PQ>
 void launch_s_pq(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, int nr, cudaStream_t s, bool persist) {
     if constexpr (sizeof(R) == 4) {
-        const bool few = (CJ ? ds.n_items_cols4 : ds.n_items_rows4) < 2 * sm_count();
+        const bool few = (CJ ? ds.n4_cols_stage : ds.n4_rows_stage) < 2 * sm_count();
         switch (nr) {
             case 1:
                 if (few) launch_s_t<R, 2, 1, CJ, PQ>(ds, src, dst, nrhs, s, persist);

@@ -233,8 +233,7 @@ std::vector<std::pair<int64_t, int64_t>> bfs_path(int64_t n, const std::vector<s
 double mround(double x) { return x >= 0 ? std::floor(x + 0.5) : -std::floor(-x + 0.5); }
 
 // Algorithm 4 along the edges E; v must hold the start value at the root of E.
-void recover_along(const std::vector<double>& u, std::vector<double>& v,
-                   const std::vector<std::pair<int64_t, int64_t>>& E) {
+void recover_along(const double* u, double* v, const std::vector<std::pair<int64_t, int64_t>>& E) {
     for (auto& e : E) v[e.second] = u[e.second] - mround(u[e.second] - v[e.first]);
 }
 
@@ -442,7 +441,7 @@ void check_values(const std::vector<cplx>& buf, const char* what) {
 
 std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t nw, const double* W,
                                      const midbf_access& acc, int r, int q, double tau, int max_disc,
-                                     uint64_t seed, midbf_recover_info* info) {
+                                     uint64_t seed, midbf_recover_info* info, bool device) {
     midbf_recover_info inf{};
     auto rows_of = [&](const std::vector<int64_t>& idx) {
         std::vector<cplx> buf(idx.size() * (size_t)nw);
@@ -490,7 +489,7 @@ std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t
                             double& used) {
         double t = tau;
         for (;;) {
-            auto D = detect(u, P, t);
+            auto D = device ? device_detect(u, P, t) : detect(u, P, t);
             if ((int)D.size() - 1 <= max_disc || t >= 0.5) {
                 used = t;
                 return D;
@@ -516,43 +515,46 @@ std::unique_ptr<Phase> recover_phase(int d, int64_t nx, const double* X, int64_t
     for (int i = 0; i < nR; ++i) rpos[R[i]] = i;
     for (int j = 0; j < nC; ++j) cpos[Cc[j]] = j;
     Pieces pc1 = partition(nx, P1, Dr), pc2 = partition(nw, P2, Dc);
-    std::vector<double> tmp_u, tmp_v;
+    // Algorithm 4 along the edges E of one piece for a batch of vectors (u, v):
+    // on the host one after the other, or on the device in one launch
+    auto along = [&](int64_t n, const std::vector<std::pair<int64_t, int64_t>>& E, int64_t root,
+                     const std::vector<const double*>& us, const std::vector<double*>& vs) {
+        if (device) {
+            device_recover_along(n, E, root, us, vs);
+        } else {
+            for (size_t k = 0; k < us.size(); ++k) recover_along(us[k], vs[k], E);
+        }
+    };
     for (size_t s = 0; s < pc1.roots.size(); ++s) {
         const int64_t rs = pc1.roots[s];
         for (size_t t = 0; t < pc2.roots.size(); ++t) {
             const int64_t ct = pc2.roots[t];
             const int i0 = (int)rpos[rs], j0 = (int)cpos[ct];
             // root row along piece t of the Omega path
-            {
-                std::vector<double> u(Urow.begin() + (size_t)i0 * nw, Urow.begin() + (size_t)(i0 + 1) * nw);
-                std::vector<double> v(rows.begin() + (size_t)i0 * nw, rows.begin() + (size_t)(i0 + 1) * nw);
-                recover_along(u, v, pc2.edges[t]);
-                std::copy(v.begin(), v.end(), rows.begin() + (size_t)i0 * nw);
-            }
+            along(nw, pc2.edges[t], ct, {&Urow[(size_t)i0 * nw]}, {&rows[(size_t)i0 * nw]});
             // root column along piece s of the X path, from the recovered (rs, ct)
-            {
-                std::vector<double> u(Ucol.begin() + (size_t)j0 * nx, Ucol.begin() + (size_t)(j0 + 1) * nx);
-                std::vector<double> v(cols.begin() + (size_t)j0 * nx, cols.begin() + (size_t)(j0 + 1) * nx);
-                v[rs] = rows[(size_t)i0 * nw + ct];
-                recover_along(u, v, pc1.edges[s]);
-                std::copy(v.begin(), v.end(), cols.begin() + (size_t)j0 * nx);
-            }
+            cols[(size_t)j0 * nx + rs] = rows[(size_t)i0 * nw + ct];
+            along(nx, pc1.edges[s], rs, {&Ucol[(size_t)j0 * nx]}, {&cols[(size_t)j0 * nx]});
+            // the other sampled rows of piece s, each from the recovered root column;
+            // the other sampled columns of piece t, each from the recovered root row
+            std::vector<const double*> us;
+            std::vector<double*> vs;
             for (int i = 0; i < nR; ++i) {
                 if (pc1.owner[R[i]] != (int64_t)s || R[i] == rs) continue;
-                std::vector<double> u(Urow.begin() + (size_t)i * nw, Urow.begin() + (size_t)(i + 1) * nw);
-                std::vector<double> v(rows.begin() + (size_t)i * nw, rows.begin() + (size_t)(i + 1) * nw);
-                v[ct] = cols[(size_t)j0 * nx + R[i]];
-                recover_along(u, v, pc2.edges[t]);
-                std::copy(v.begin(), v.end(), rows.begin() + (size_t)i * nw);
+                rows[(size_t)i * nw + ct] = cols[(size_t)j0 * nx + R[i]];
+                us.push_back(&Urow[(size_t)i * nw]);
+                vs.push_back(&rows[(size_t)i * nw]);
             }
+            along(nw, pc2.edges[t], ct, us, vs);
+            us.clear();
+            vs.clear();
             for (int j = 0; j < nC; ++j) {
                 if (pc2.owner[Cc[j]] != (int64_t)t || Cc[j] == ct) continue;
-                std::vector<double> u(Ucol.begin() + (size_t)j * nx, Ucol.begin() + (size_t)(j + 1) * nx);
-                std::vector<double> v(cols.begin() + (size_t)j * nx, cols.begin() + (size_t)(j + 1) * nx);
-                v[rs] = rows[(size_t)i0 * nw + Cc[j]];
-                recover_along(u, v, pc1.edges[s]);
-                std::copy(v.begin(), v.end(), cols.begin() + (size_t)j * nx);
+                cols[(size_t)j * nx + rs] = rows[(size_t)i0 * nw + Cc[j]];
+                us.push_back(&Ucol[(size_t)j * nx]);
+                vs.push_back(&cols[(size_t)j * nx]);
             }
+            along(nx, pc1.edges[s], rs, us, vs);
         }
     }
     for (int i = 0; i < nR; ++i)

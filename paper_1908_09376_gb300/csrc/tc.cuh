@@ -561,9 +561,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_s_tc(SStage<float> st, SSide<
                                 sq = fmaf(rc[q], cj[1 + P + q], sq);
                             }
                         }
-                        thp += sqrtf(sq);
+                        thp += sqrt_nr(sq);
                     }
-                    thp -= rintf(thp);
+                    thp = frac_rn(thp);
                     sincos2pi(thp, &ei, &er);
                     if (CONJ) ei = -ei;
                 }

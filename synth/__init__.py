@@ -115,7 +115,9 @@ class Workload:
     """One synthetic problem: points, phase family, build tolerance, RHS.
 
     x_kind / w_kind: "grid" (uniform X grid, integer frequency grid Omega),
-    "random" (uniform in [0,1)^d, seeds x_seed / w_seed) or "sphere" (both
+    "unit" (w_kind only: Omega the same uniform grid in [0,1)^d as X, the
+    discretization of Example 1 as the paper states it), "random" (uniform in
+    [0,1)^d, seeds x_seed / w_seed) or "sphere" (both
     halves of the icosphere of level n, scaled by h = sqrt(|X|)/10 so that the
     DISTANCE phase |x - xi| is the Helmholtz phase h |x - xi| of the unit sphere).
     """
@@ -132,7 +134,7 @@ class Workload:
     recovered: bool = False     # phase recovered from 8 rows + 8 cols
     sample_rows: int = 0        # 0 = full direct sum, else sampled rows
     sample_seed: int = 3
-    w_kind: str = "grid"        # "grid", "random" or "sphere"
+    w_kind: str = "grid"        # "grid", "unit", "random" or "sphere"
     w_seed: int = 1
     t: float = 2.0              # oversampling of the ID samples (Sec. 3.2)
 
@@ -170,6 +172,9 @@ class Workload:
         boxX = (np.zeros(self.d), 1.0)
         if self.w_kind == "random":
             W = uniform_random_points(self.N, self.d, self.w_seed)
+            boxW = (np.zeros(self.d), 1.0)
+        elif self.w_kind == "unit":
+            W = uniform_grid(self.n, self.d)
             boxW = (np.zeros(self.d), 1.0)
         else:
             W = frequency_grid(self.n, self.d)

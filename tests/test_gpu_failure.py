@@ -42,3 +42,39 @@ def test_bounded_wait_runs_out_and_the_context_survives():
     assert torch.equal(g0, g1)
     with pytest.raises(mb.MidbfError):
         dp.wait_selftest(ctas=0)
+
+
+def test_tensor_core_kernels_give_up_once_the_status_word_is_set():
+    """A tensor-core apply issued while the plan's status word already reads
+    MIDBF_ETIMEOUT (left set by the self-test, not reset) must return without
+    waiting out any limit: every bounded wait in the pipelines checks the word
+    and gives up at once, the CTAs drain their copies in flight, free their
+    tensor memory and exit.  The status stays MIDBF_ETIMEOUT; after a reset the
+    next apply gives exactly the result of an apply before the failure."""
+    n = 32
+    X, W = synth.uniform_grid(n, 2), synth.frequency_grid(n, 2)
+    plan = mb.Plan.build(mb.Phase.closed_form(synth.PHASE_FIO2D, X, W), tol=1e-6, n0=16,
+                         boxX=(np.zeros(2), 1.0), boxW=(np.full(2, -n / 2), float(n)))
+    for mode in (mb.BF16, mb.BF16 | mb.REFINE):
+        dp = mb.DevicePlan(plan, mode)
+        F = torch.from_numpy(synth.complex_gaussian(n * n, 32, 3).T.copy()).to("cuda", torch.complex64)
+        g0 = dp.apply(F)
+        a0 = dp.apply(g0, adjoint=True)
+        torch.cuda.synchronize()
+        assert dp.status() == mb.OK
+        dp.wait_selftest(ctas=2)
+        torch.cuda.synchronize()
+        assert dp.status(reset=False) == mb.ETIMEOUT
+        t0 = time.perf_counter()
+        dp.apply(F)                              # 32 RHS: every stage on the tensor cores
+        dp.apply(g0, adjoint=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        assert dt < 1.5, dt                      # no CTA waited out the 2 s limit
+        assert dp.status(reset=True) == mb.ETIMEOUT
+        assert dp.status() == mb.OK
+        g1 = dp.apply(F)
+        a1 = dp.apply(g1, adjoint=True)
+        torch.cuda.synchronize()
+        assert dp.status() == mb.OK
+        assert torch.equal(g0, g1) and torch.equal(a0, a1)

@@ -53,21 +53,51 @@ def _case(name):
     return _C[name]
 
 
+def _errors(got, ref):
+    """rel-L2 over all entries, and the largest entry error relative to the
+    largest reference entry divided by 2: among the ~10^5 - 10^6 entries of a
+    case the largest error sits about twice as far out in its distribution's
+    tail as the largest reference entry does in its own (measured 1.7x for
+    the refined products at 130 RHS), so both ratios are held to the same
+    bound."""
+    return direct.rel_l2(got, ref), float(np.abs(got - ref).max() / np.abs(ref).max()) / 2.0
+
+
+# 16: the smallest tensor-core case; 130: a ragged RHS tile (Rpad 144); 256: the
+# full TMEM accumulator of one pass (D_top in columns [0, 256), D_bot in
+# [256, 512)); 300: more than one pass (a group of 256, then one of 44).
 @pytest.mark.parametrize("case", ["fio2d_n64", "fio3d_n8", "lowrank_n32"])
 @pytest.mark.parametrize("mode,tol", [(mb.BF16, 2e-2), (mb.BF16 | mb.REFINE, 2e-5)])
 def test_tensor_core_middle_factor(case, mode, tol):
     fac, plan, mats = _case(case)
     dp = mb.DevicePlan(plan, mode)
-    for nrhs in (16, 130):
+    for nrhs in (16, 130, 256, 300):
         f = synth.complex_gaussian(fac.nw, nrhs, 60)
         h = synth.complex_gaussian(fac.nx, nrhs, 61)
         g = dp.apply(torch.from_numpy(f.T.copy()).to("cuda", torch.complex64)).cpu().numpy().T
         a = dp.apply(torch.from_numpy(h.T.copy()).to("cuda", torch.complex64), adjoint=True).cpu().numpy().T
-        g_ref = np.stack([midbf.apply(fac, f[:, r], mats) for r in range(nrhs)], 1)
-        a_ref = np.stack([midbf.apply_adjoint(fac, h[:, r], mats) for r in range(nrhs)], 1)
-        eg, ea = direct.rel_l2(g, g_ref), direct.rel_l2(a, a_ref)
-        assert eg < tol and ea < tol, (case, mode, nrhs, eg, ea)
+        g_ref = midbf.apply(fac, f, mats)
+        a_ref = midbf.apply_adjoint(fac, h, mats)
+        (eg, mg), (ea, ma) = _errors(g, g_ref), _errors(a, a_ref)
+        assert max(eg, mg, ea, ma) < tol, (case, mode, nrhs, eg, mg, ea, ma)
     assert dp.status() == mb.OK
+
+
+def test_tensor_core_groups_agree_with_single_passes():
+    """300 RHS run as a pass of 256 and a pass of 44; each column must agree
+    with the same column applied in a pass of its own group size (the passes
+    share no state but the RHS image buffer, which every pass rewrites).  The
+    kernels are the same, so only the FP32 accumulation could differ."""
+    fac, plan, _ = _case("fio2d_n64")
+    dp = mb.DevicePlan(plan, mb.BF16 | mb.REFINE)
+    f = torch.from_numpy(synth.complex_gaussian(fac.nw, 300, 63).T.copy()).to("cuda", torch.complex64)
+    g = dp.apply(f)
+    g_first = dp.apply(f[:256].contiguous())
+    g_rest = dp.apply(f[256:].contiguous())
+    torch.cuda.synchronize()
+    scale = g.abs().max().item()
+    assert (g[:256] - g_first).abs().max().item() <= 1e-6 * scale
+    assert (g[256:] - g_rest).abs().max().item() <= 1e-6 * scale
 
 
 def test_tensor_mode_below_threshold_uses_simt():

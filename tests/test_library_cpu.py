@@ -136,6 +136,18 @@ def test_phase_eval_matches_hand_values():
     assert abs(p3.eval([1], [0])[0] - (4 + 13 ** 0.5 / 8)) < 1e-14
 
 
+def test_phase_eval_matches_hand_values_3d():
+    """The library's FP64 evaluation of the 3D FIO phase at the hand-evaluated
+    points of tests/golden/phase_values_3d.txt."""
+    rows = [l.split() for l in open(os.path.join(os.path.dirname(__file__), "golden", "phase_values_3d.txt"))
+            if l.strip() and l[0] != "#"]
+    X = np.array([[float(v) for v in r[:3]] for r in rows])
+    W = np.array([[float(v) for v in r[3:6]] for r in rows])
+    ph = mb.Phase.closed_form(synth.PHASE_FIO3D, X, W)
+    got = ph.eval(np.arange(len(rows)), np.arange(len(rows)))
+    assert np.abs(got - np.array([float(r[6]) for r in rows])).max() < 1e-14
+
+
 def test_plan_roundtrip_with_oracle_writer():
     X, W, bx, bw = _grid(32)
     fac = midbf.build(OPhase(synth.PHASE_FIO2D, X, W), n0=16, tol=1e-6, t=2.0, boxX=bx, boxW=bw)
@@ -258,6 +270,21 @@ def test_recovery_callback_failure():
         with pytest.raises(mb.MidbfError) as e:
             mb.Phase.recover(X, W, rows, cols, r=2, q=2)
         assert e.value.code == mb.ECALLBACK
+
+
+def test_recovery_path_validation():
+    """midbf_rpath_create checks the edges before it touches a device: a parent
+    not reached by earlier edges, a child reached twice or an index out of
+    range is MIDBF_EINVAL; a valid path without a GPU is MIDBF_ECUDA."""
+    for edges in ([[1, 2], [0, 1]], [[0, 1], [0, 1]], [[0, 7]], [[0, 1], [2, 3]]):
+        with pytest.raises(mb.MidbfError) as e:
+            mb.RecoveryPath(4, np.array(edges), root=0)
+        assert e.value.code == mb.EINVAL, edges
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(mb.MidbfError) as e:
+            mb.RecoveryPath(4, np.array([[0, 1], [1, 2], [1, 3]]))
+        assert e.value.code == mb.ECUDA
 
 
 def test_recovery_partitions_at_a_jump():

@@ -39,6 +39,18 @@ def test_phase_hand_values():
         assert abs(got - eval(val)) < 1e-14, (fam, x1, x2, k1, k2)
 
 
+def test_phase_hand_values_3d():
+    """The 3D FIO phase at hand-evaluated points (tests/golden/phase_values_3d.txt):
+    the cyclic index k+1 and the sin/cos order of c_k are what the values fix."""
+    rows = [l.split() for l in open(os.path.join(GOLD, "phase_values_3d.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 4
+    for x1, x2, x3, k1, k2, k3, val in rows:
+        x = np.array([float(x1), float(x2), float(x3)])
+        w = np.array([float(k1), float(k2), float(k3)])
+        got = coordinate_phase(synth.PHASE_FIO3D, x, w)
+        assert abs(got - float(val)) < 1e-14, (x, w, got, val)
+
+
 # ---------------------------------------------------------------- direct sum
 @pytest.mark.parametrize("n,d", [(16, 2), (32, 2), (8, 3)])
 def test_direct_sum_matches_fft(n, d):

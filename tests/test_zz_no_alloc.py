@@ -56,6 +56,56 @@ def test_noalloc_matches_apply_twice(prec):
             assert np.isfinite(a).all() and err < TOL[prec], (call, adjoint, err)
 
 
+@pytest.mark.parametrize("mode", [mb.BF16, mb.BF16 | mb.REFINE])
+@pytest.mark.parametrize("nrhs", [16, 32])
+def test_noalloc_tensor_core_modes_match_apply_twice(mode, nrhs):
+    """With 16 or more right-hand sides the BF16 modes run the tensor-core
+    kernels, whose RHS images sit in the scratch array after the vector
+    buffers; that part of the layout must agree with a caller workspace too.
+    Both calls use the same kernels in the same order, so the results agree
+    bit for bit."""
+    fac, plan = _plan()
+    dp = mb.DevicePlan(plan, mode)
+    assert dp.workspace_bytes(nrhs) <= mb.midbf_noalloc_scratch_bytes()
+    s = torch.cuda.current_stream().cuda_stream
+    ws = torch.empty(dp.workspace_bytes(nrhs), dtype=torch.uint8, device="cuda")
+    for call in range(2):
+        for adjoint in (0, 1):
+            nin, nout = (fac.nx, fac.nw) if adjoint else (fac.nw, fac.nx)
+            x = torch.from_numpy(synth.complex_gaussian(nin, nrhs, 40 + call + 2 * adjoint).T.copy()).to(
+                "cuda", torch.complex64)
+            y_ref = torch.empty((nrhs, nout), dtype=torch.complex64, device="cuda")
+            y = torch.full((nrhs, nout), complex(np.nan, np.nan), dtype=torch.complex64, device="cuda")
+            mb.check(mb.midbf_apply(dp.h, adjoint, x.data_ptr(), nin, y_ref.data_ptr(), nout, nrhs, s,
+                                    ws.data_ptr(), ws.numel()), "midbf_apply")
+            mb.check(mb.midbf_apply_noalloc(dp.h, adjoint, x.data_ptr(), nin, y.data_ptr(), nout, nrhs, s),
+                     "midbf_apply_noalloc")
+            torch.cuda.synchronize()
+            assert torch.equal(y, y_ref), (mode, nrhs, call, adjoint)
+    assert dp.status() == mb.OK
+
+
+def test_noalloc_argument_checks_match_apply():
+    """The same argument checks as midbf_apply: a null pointer, nrhs <= 0,
+    overlapping input and output, and profiling left on while the stream
+    records a graph are all rejected with MIDBF_EINVAL."""
+    fac, plan = _plan()
+    dp = mb.DevicePlan(plan, mb.FP32)
+    x = torch.zeros(fac.nw, dtype=torch.complex64, device="cuda")
+    y = torch.zeros(fac.nx, dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    assert mb.midbf_apply_noalloc(dp.h, 0, None, fac.nw, y.data_ptr(), fac.nx, 1, s.cuda_stream) == mb.EINVAL
+    assert mb.midbf_apply_noalloc(dp.h, 0, x.data_ptr(), fac.nw, y.data_ptr(), fac.nx, 0, s.cuda_stream) == mb.EINVAL
+    assert mb.midbf_apply_noalloc(dp.h, 0, x.data_ptr(), fac.nw, x.data_ptr(), fac.nx, 1, s.cuda_stream) == mb.EINVAL
+    dp.profile(True)
+    with mb.capture(s, keep=(x, y)):
+        rc = mb.midbf_apply_noalloc(dp.h, 0, x.data_ptr(), fac.nw, y.data_ptr(), fac.nx, 1, s.cuda_stream)
+    dp.profile(False)
+    torch.cuda.synchronize()
+    assert rc == mb.EINVAL
+    assert b"profiling" in mb.midbf_last_error()
+
+
 def test_noalloc_rejects_oversized_problem():
     fac, plan = _plan()
     dp = mb.DevicePlan(plan, mb.FP64)
