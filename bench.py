@@ -113,6 +113,37 @@ def aggregate(total_ms_local, units_per_step_per_rank, steps, pg=None, device=No
     return ms_per_step, world * units_per_step_per_rank / (ms_per_step * 1e-3)
 
 
+def aggregate_sharded(total_ms_local, units_local, steps, pg=None, device=None):
+    """Whole-job throughput when the ranks share one batch of instances (no
+    replicas): the step time is the slowest rank's, the units are the sum of
+    every rank's own instances."""
+    total_ms, units = float(total_ms_local), float(units_local)
+    if pg is not None:
+        import torch
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        uu = torch.tensor([units], dtype=torch.float64, device=device)
+        pg.all_reduce(tt, op=pg.ReduceOp.MAX)
+        pg.all_reduce(uu, op=pg.ReduceOp.SUM)
+        total_ms, units = tt.item(), uu.item()
+    ms_per_step = total_ms / steps
+    return ms_per_step, units / (ms_per_step * 1e-3)
+
+
+def shard_instances(work, world, rank):
+    """Indices of the instances rank `rank` of `world` applies: the instances
+    in decreasing order of work, each to the rank with the least work so far
+    (ties to the lower rank).  Every instance goes to exactly one rank and no
+    data moves between ranks: the instances are independent problems."""
+    load = [0.0] * world
+    mine = []
+    for i in sorted(range(len(work)), key=lambda i: (-work[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += work[i]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
 def pick_workload(args):
     """The synthetic workload, its RHS count, arithmetic and build site."""
     if args.workload == "fio2d":
@@ -374,6 +405,11 @@ def main_batched(args, ws, rank, dev, pg):
     insts = [w if w.n <= 256 else synth.Workload(w.name.replace("_n512", "_n256"), w.d, 256, w.phase, w.tol, w.n0,
                                                  w.nrhs, w.f_seed, sample_rows=256, sample_seed=w.sample_seed)
              for w in synth.batched_instances(32, 1)]
+    n_all = len(insts)
+    if ws > 1:
+        # the batch is shared out: each rank builds and applies its own instances
+        # (work ~ points x RHS), no exchange between ranks
+        insts = [insts[i] for i in shard_instances([w.N * w.nrhs for w in insts], ws, rank)]
     t0 = time.perf_counter()
     dps, phs, n0s = [], [], []
     for w in insts:
@@ -427,7 +463,7 @@ def main_batched(args, ws, rank, dev, pg):
         pg.barrier()
     clk = clocks.stop()
     units = sum(2 * w.N * w.nrhs for w in insts)
-    ms_per_step, value = aggregate(sum(a.elapsed_time(b) for a, b in ev), units, args.steps, pg, dev)
+    ms_per_step, value = aggregate_sharded(sum(a.elapsed_time(b) for a, b in ev), units, args.steps, pg, dev)
 
     # algorithmic bytes of one step: every instance's stages, forward and adjoint
     total_bytes = 0.0
@@ -471,7 +507,8 @@ def main_batched(args, ws, rank, dev, pg):
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - te) / ke
     io_bytes = sum(x.numel() * 8 for x in xs)
-    e2e = {"value": ws * units / e2e_s, "unit": "points*RHS/s", "h2d_bytes_per_step": io_bytes,
+    _, e2e_value = aggregate_sharded(e2e_s * 1e3, units, 1, pg, dev)
+    e2e = {"value": e2e_value, "unit": "points*RHS/s", "h2d_bytes_per_step": io_bytes,
            "d2h_bytes_per_step": io_bytes, "ms_per_step": round(e2e_s * 1e3, 4)}
     launches = mb.batched_launches(sel, adj, nr)
     counts = {}
@@ -479,13 +516,15 @@ def main_batched(args, ws, rank, dev, pg):
         counts[w.n] = counts.get(w.n, 0) + 1
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-           "config": {"workload": "batched32_fio2d_n_le_256", "instances": len(insts), "n_counts": counts,
+           "scaling": "strong" if ws > 1 else "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+           "config": {"workload": "batched32_fio2d_n_le_256", "instances": n_all, "instances_on_rank0": len(insts),
+                      "n_counts": counts,
                       "nrhs": [w.nrhs for w in insts], "points_rhs_per_step": units, "mode": "fp32",
                       "step": "forward + adjoint of every instance in one midbf_apply_batched call",
                       "tol": 1e-6, "n0": n0s, "build": "device", "store": "fp32", "autotuned": True,
                       "build_s": round(t_build, 1), "tune_s": round(t_tune, 1),
-                      "l2": "flushed (512 MB write) between timed steps", "parallelism": f"replicas x{ws}"},
+                      "l2": "flushed (512 MB write) between timed steps",
+                      "parallelism": f"instances shared out over {ws} ranks" if ws > 1 else "one GPU"},
            "roofline": roofline, "rel_l2_direct_sampled": {"max_forward": max(e["forward"] for e in errs) if errs else None,
                                                            "max_adjoint": max(e["adjoint"] for e in errs) if errs else None,
                                                            "rows": 32, "per_instance": errs},
@@ -728,7 +767,25 @@ def main():
     units = (nx + nw) * R1                  # outputs of the forward and the adjoint apply
     ms_per_step, value = aggregate(sum(step_ms), units, args.steps, pg, dev)
 
-    # the same steps again with CUDA events around every stage launch
+    # the same step with the middle factor and its U stage one after the other
+    overlap_chunks = dp32.overlap()
+    no_overlap = None
+    if overlap_chunks > 1 and not use_graph:
+        dp32.set_overlap(False)
+        t_off = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.zero_()
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            step()
+            e_b.record(stream)
+            torch.cuda.synchronize()
+            t_off.append(e_a.elapsed_time(e_b))
+        dp32.set_overlap(True)
+        no_overlap = {"ms_per_step": round(statistics.mean(t_off), 5), "chunks": overlap_chunks,
+                      "speedup_of_overlap": round(statistics.mean(t_off) / ms_per_step, 3)}
+    # the same steps again with CUDA events around every stage launch (profiling runs the
+    # stages one after the other, without the overlap)
     dp32.profile(True)
     stage_ms = {}
     for i in range(args.steps):
@@ -769,7 +826,8 @@ def main():
     # reciprocal square root; the SFU completes 16 operations per clock per SM
     sfu_ops = 3 if wl.phase in (synth.PHASE_FIO2D, synth.PHASE_FIO3D, synth.PHASE_FIO2D_JUMP,
                                 synth.PHASE_DISTANCE) and not wl.recovered else 2
-    sfu_peak = 152 * 16 * 2.07e9 / sfu_ops / 1e9    # G entries/s at the maximum SM clock
+    fma_rate, sfu_rate = mb.pipe_rates(stream)      # measured on this GPU (midbf_pipe_rates)
+    sfu_peak = sfu_rate / sfu_ops / 1e9             # G entries/s
     s_entries_of = {q_: sinfo[q_][1] for q_ in range(ns) if sinfo[q_][0] == 1}
 
     def hbm_roofline(exclude_s):
@@ -795,8 +853,10 @@ def main():
         roofline = {"bound": "alu", "achieved": round(achieved, 1), "peak": round(sfu_peak, 1), "unit": "Gentries/s",
                     "frac": round(achieved / sfu_peak, 4), "traffic": None,
                     "kernel": f"{direction} stage {q} (S, made on the fly)",
-                    "peak_source": (f"derived: 152 SMs x 16 SFU ops/clk x 2.07 GHz / {sfu_ops} (SFU operations per "
-                                    "entry: sine, cosine" + (", reciprocal square root)" if sfu_ops == 3 else ")"))}
+                    "peak_source": (f"measured SFU rate {sfu_rate / 1e12:.3f}e12 ops/s (midbf_pipe_rates) / {sfu_ops} "
+                                    "SFU operations per entry (sine, cosine" +
+                                    (", reciprocal square root)" if sfu_ops == 3 else ")")),
+                    "fma_rate_per_s": fma_rate, "sfu_rate_per_s": sfu_rate}
         roofline_hbm = hbm_roofline(True)
         roofline_hbm["whole_step_GBps"] = round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1)
     else:
@@ -903,6 +963,36 @@ def main():
                                 "s_mode": "stored", "bound": "alu(fp64)"}
         extras["speedup_mixed_vs_plain"] = round(ms64 / ms_per_step, 3)
         extras["rel_l2_fp32_vs_fp64"] = {"forward": rel_fwd, "adjoint": rel_adj}
+        # the mixed form with the accurate phase (double-FP32 middle-factor phases)
+        dpdf = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY_DF)
+        gdf = torch.empty_like(g)
+        hdf = torch.empty_like(h)
+        wsdf = torch.empty(dpdf.workspace_bytes(1), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            dpdf.apply(f, out=gdf, workspace=wsdf)
+            dpdf.apply(gdf, adjoint=True, out=hdf, workspace=wsdf)
+        torch.cuda.synchronize()
+        totdf = 0.0
+        for _ in range(k64):
+            flush.zero_()
+            e0.record(stream)
+            dpdf.apply(f, out=gdf, workspace=wsdf)
+            dpdf.apply(gdf, adjoint=True, out=hdf, workspace=wsdf)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            totdf += e0.elapsed_time(e1)
+        msdf = totdf / k64
+        dpdf.apply(f, out=gdf, workspace=wsdf)
+        dpdf.apply(g, adjoint=True, out=hdf, workspace=wsdf)   # the adjoint of the same input as h64
+        torch.cuda.synchronize()
+        extras["fp32_accurate_phase"] = {
+            "value": 2 * N / (msdf * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msdf, 4),
+            "s_mode": "on the fly, double-FP32 phase (MIDBF_S_ONTHEFLY_DF)",
+            "rel_l2_vs_fp64": {
+                "forward": (torch.linalg.vector_norm(gdf.to(torch.complex128) - g64) / torch.linalg.vector_norm(g64)).item(),
+                "adjoint": (torch.linalg.vector_norm(hdf.to(torch.complex128) - h64) / torch.linalg.vector_norm(h64)).item()},
+            "speedup_vs_plain": round(ms64 / msdf, 3)}
+        del dpdf, wsdf, gdf, hdf
         del dp64, ws64
         torch.cuda.empty_cache()
         # 64 right-hand sides, FP32
@@ -1039,6 +1129,9 @@ def main():
                       "parallelism": f"replicas x{ws}", "build_s": round(t_build, 1),
                       "upload_s": round(t_up, 1)},
            "roofline": roofline, "roofline_hbm": roofline_hbm, "stages": stage_rows, "rel_l2_direct_sampled": acc,
+           "overlap": {"chunks": overlap_chunks, "without": no_overlap,
+                       "note": "middle factor and its U stage run chunk by chunk on two streams (midbf_dplan_set_overlap)"},
+           "pipe_rates": {"fma_per_s": fma_rate, "sfu_per_s": sfu_rate, "source": "midbf_pipe_rates, measured"},
            "clocks": clk, "e2e": e2e,
            "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
     out.update(extras)

@@ -72,6 +72,12 @@ extern "C" {
 /* ---- middle-factor modes ----------------------------------------------- */
 #define MIDBF_S_ONTHEFLY 0  /* S entries exp(2 pi i Phi) generated in the kernel */
 #define MIDBF_S_STORED   1  /* S entries precomputed once at dplan creation      */
+#define MIDBF_S_ONTHEFLY_DF 2 /* on the fly with the accurate phase (MIDBF_FP32 plans,
+                           inner-product phases): the phase of every entry in
+                           double-FP32 arithmetic (TwoSum / TwoProduct error-free
+                           transformations), so its rounding no longer grows with
+                           the phase's magnitude; about 3x the middle factor's
+                           arithmetic.  Not taken by midbf_apply_batched.       */
 
 typedef struct midbf_phase midbf_phase;  /* phase function over (X, Omega)   */
 typedef struct midbf_plan midbf_plan;    /* host butterfly factors (immutable) */
@@ -268,6 +274,9 @@ int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_
  * MIDBF_EINVAL.  Errors as midbf_dplan_create, and MIDBF_EINVAL for unknown
  * flags or an already consumed plan. */
 #define MIDBF_DPLAN_CONSUME 1
+/* MIDBF_DPLAN_OVERLAP: prepare the overlap of the middle factor with the U
+ * stage after it (see midbf_dplan_set_overlap below) and switch it on. */
+#define MIDBF_DPLAN_OVERLAP 2
 int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags, midbf_dplan** out);
 void midbf_dplan_destroy(midbf_dplan* dp);
 
@@ -343,9 +352,9 @@ int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adj
  * The middle factor S (Sec. 3.5) is bound by arithmetic (its entries are
  * made on the fly), the U stage after it by memory.  Each U block reads the
  * outputs of a few S blocks only, and these blocks fall into independent
- * groups; midbf_dplan_create deals the groups into (up to 4) chunks.  With
- * the overlap on (the default when a plan has at least two groups), an apply
- * on the SIMT kernels runs S and that U stage chunk by chunk: forward, chunk
+ * groups; midbf_dplan_create_ex with MIDBF_DPLAN_OVERLAP deals the groups
+ * into (up to 4) chunks.  With the overlap on, an apply on the SIMT kernels
+ * runs S and that U stage chunk by chunk: forward, chunk
  * k of S on the caller's stream and chunk k of U, after an event, on a side
  * stream of the plan; adjoint, U's adjoint chunk first and S's adjoint chunk
  * on the side stream.  The side stream forks from the caller's stream before
@@ -355,7 +364,11 @@ int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adj
  * (midbf_dplan_profile times each stage alone) and for stages on the tensor
  * cores.  Applies of one plan from several host threads are serialized while
  * they issue the overlapped pair.  Plans with chunks need a third internal
- * vector in the workspace (midbf_workspace_size includes it).
+ * vector in the workspace (midbf_workspace_size includes it).  Measured on
+ * one GB300 at n = 256, one RHS, the overlap is slower (2.00 ms per forward
+ * + adjoint step against 1.85 ms): each chunk's launch leaves a partial wave
+ * of CTAs, and S and U do not co-reside enough to win it back, so plans are
+ * created without it.
  * midbf_dplan_set_overlap: enable = 1 on (if the plan has chunks), 0 off.
  * midbf_dplan_overlap: the chunk count in force (0: off).  EINVAL on null
  * arguments. */
@@ -448,6 +461,15 @@ int midbf_stage_times(const midbf_dplan* dp, int max_stages, float* ms, int* kin
  * to *n_stages.  Host-only; no device work.  EINVAL on a null plan or count. */
 int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t* entries, int64_t* dense,
                      int* n_stages);
+
+/* Measured arithmetic rates of the current device (for rooflines of the
+ * kernels bound by arithmetic): FP32 fused multiply-adds per second (eight
+ * independent chains per thread) and SFU operations per second (chains of
+ * rsqrt.approx), both over every SM, best of three timed launches on stream.
+ * Allocates a small device buffer and synchronizes.  The paper has no
+ * counterpart: this is measurement support.  Errors: MIDBF_EINVAL,
+ * MIDBF_ECUDA. */
+int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per_s);
 
 /* midbf_apply_noalloc: midbf_apply for callers that cannot allocate device
  * memory when they apply the operator - for example a service whose GPU

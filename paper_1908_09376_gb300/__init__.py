@@ -27,7 +27,7 @@ CHOICE_DEFAULT, CHOICE_COLUMN1, CHOICE_PERSIST, CHOICE_TENSOR = 0, 32, 256, 1024
 PHASE_FIO2D, PHASE_FIO3D, PHASE_FIO2D_JUMP, PHASE_DOT, PHASE_ZERO, PHASE_SEPARABLE, PHASE_LOWRANK = 1, 2, 3, 4, 5, 6, 7
 PHASE_DISTANCE = 8
 FP64, FP32, BF16, REFINE = 0, 1, 2, 16
-S_ONTHEFLY, S_STORED = 0, 1
+S_ONTHEFLY, S_STORED, S_ONTHEFLY_DF = 0, 1, 2
 
 _i64p = C.POINTER(C.c_int64)
 _dblp = C.POINTER(C.c_double)
@@ -102,6 +102,7 @@ midbf_free = _sig("midbf_free", None, [_vp])
 midbf_dplan_create = _sig("midbf_dplan_create", C.c_int, [_vp, C.c_int, C.c_int, C.POINTER(_vp)])
 midbf_dplan_create_ex = _sig("midbf_dplan_create_ex", C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.POINTER(_vp)])
 DPLAN_CONSUME = 1
+DPLAN_OVERLAP = 2
 midbf_dplan_destroy = _sig("midbf_dplan_destroy", None, [_vp])
 midbf_workspace_size = _sig("midbf_workspace_size", C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)])
 midbf_dplan_bytes = _sig("midbf_dplan_bytes", C.c_int, [_vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)])
@@ -135,6 +136,16 @@ midbf_apply_batched = _sig("midbf_apply_batched", C.c_int,
 midbf_apply_noalloc = _sig("midbf_apply_noalloc", C.c_int,
                            [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp])
 midbf_noalloc_scratch_bytes = _sig("midbf_noalloc_scratch_bytes", C.c_size_t, [])
+midbf_pipe_rates = _sig("midbf_pipe_rates", C.c_int, [_vp, _dblp, _dblp])
+
+
+def pipe_rates(stream=None):
+    """(FP32 FMAs per second, SFU operations per second) measured on the current device."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    a, b = C.c_double(), C.c_double()
+    check(midbf_pipe_rates(s.cuda_stream, C.byref(a), C.byref(b)), "midbf_pipe_rates")
+    return a.value, b.value
 
 EXPORTED = [n for n in dir() if n.startswith("midbf_") and callable(globals()[n])
             and not isinstance(globals()[n], type)]
@@ -356,12 +367,13 @@ class Plan:
 class DevicePlan:
     """Owns a midbf_dplan (plan resident on the current CUDA device)."""
 
-    def __init__(self, plan: Plan, precision=FP32, s_mode=S_ONTHEFLY, consume=False):
+    def __init__(self, plan: Plan, precision=FP32, s_mode=S_ONTHEFLY, consume=False, overlap=False):
         """consume=True releases the host plan's coefficients as they are uploaded
-        (midbf_dplan_create_ex with MIDBF_DPLAN_CONSUME)."""
+        (midbf_dplan_create_ex with MIDBF_DPLAN_CONSUME); overlap=True prepares the
+        overlap of the middle factor with the U stage after it (MIDBF_DPLAN_OVERLAP)."""
         h = _vp()
-        check(midbf_dplan_create_ex(plan.h, precision, s_mode, DPLAN_CONSUME if consume else 0, C.byref(h)),
-              "midbf_dplan_create_ex")
+        flags = (DPLAN_CONSUME if consume else 0) | (DPLAN_OVERLAP if overlap else 0)
+        check(midbf_dplan_create_ex(plan.h, precision, s_mode, flags, C.byref(h)), "midbf_dplan_create_ex")
         self.h = h
         self.mode = precision
         self.precision = FP64 if precision == FP64 else FP32   # storage precision of the vectors

@@ -20,7 +20,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmidbf.so")
 
 HOST = ["capi.cpp", "phase.cpp", "plan.cpp", "qr.cpp", "build.cpp", "recover.cpp"]
-CUDA = ["device.cu", "launch_rc.cu", "launch_s.cu", "launch_tc.cu", "batched.cu", "build_gpu.cu", "recover_gpu.cu"]
+CUDA = ["device.cu", "launch_rc.cu", "launch_s.cu", "launch_tc.cu", "batched.cu", "build_gpu.cu", "recover_gpu.cu",
+        "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -114,7 +114,7 @@ void launch_batch_group(const midbf_dplan* const* dps, const std::array<int, 4>&
             sm = std::max(sm, pattern_r_smem<R>(ds.max_nred, rt, nr));
         } else if (type == BT_C1) {
             items += ds.n_items_c1;
-            sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1));
+            sm = std::max(sm, pattern_c1_smem<R>(ds.max_narrow, ds.max_nsub));
         } else {
             items += ds.n_items_c;
             sm = std::max(sm, pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, nr));
@@ -202,7 +202,7 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
                 if (use_r) {
                     const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
                     key = {BT_R, ds.rt, t, 0};
-                } else if (nr == 1 && force == 0 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
+                } else if (nr == 1 && force == 0 && pattern_c1_smem<R>(ds.max_narrow, ds.max_nsub) <= kSmemCap) {
                     key = {BT_C1, 0, 1, 0};
                 } else {
                     const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC, qq); });

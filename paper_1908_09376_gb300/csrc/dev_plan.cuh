@@ -80,6 +80,7 @@ struct DevStage : DevStageBase {
     int n_items_rows = 0, n_items_cols = 0, n_items_rows4 = 0, n_items_cols4 = 0, rt_rows = 1, rt_cols = 1;
     int n4_rows_stage = 0, n4_cols_stage = 0;   // 128-row items of the whole stage (item-size rule)
     bool s_dist = false;                // square-root term in the distance form (DISTANCE phase)
+    bool s_df = false;                  // accurate phase: double-FP32 (MIDBF_S_ONTHEFLY_DF)
     // tensor-core modes: dense BF16 tile images of the V/U blocks,
     // [0] forward orientation (stage input -> output), [1] adjoint
     bool tc = false;

@@ -520,6 +520,8 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     if (P > 8 || Q > 3) fail(MIDBF_EINVAL, "on-the-fly middle factor supports at most 8 low-rank terms");
     std::vector<int> blk_rows, blk_cols, blk_nrow, blk_ncol, rpos, cpos;
     std::vector<R> ra, ru, rc, ca, cu, cc;
+    std::vector<double> da_r, du_r, dc_r, da_c, du_c, dc_c;   // the FP64 values (accurate phase only)
+    const bool keep64 = dp->s_mode == MIDBF_S_ONTHEFLY_DF;
     std::vector<int2> it_rows, it_cols, it_rows4, it_cols4;
     int maxr = 1, maxc = 1;
     for (size_t b = 0; b < st.blocks.size(); ++b) {
@@ -538,6 +540,14 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
         for (double v : c.a) ca.push_back((R)v);
         for (double v : c.u) cu.push_back((R)v);
         for (double v : c.c) cc.push_back((R)v);
+        if (keep64) {
+            da_r.insert(da_r.end(), r.a.begin(), r.a.end());
+            du_r.insert(du_r.end(), r.u.begin(), r.u.end());
+            dc_r.insert(dc_r.end(), r.c.begin(), r.c.end());
+            da_c.insert(da_c.end(), c.a.begin(), c.a.end());
+            du_c.insert(du_c.end(), c.u.begin(), c.u.end());
+            dc_c.insert(dc_c.end(), c.c.begin(), c.c.end());
+        }
         for (int64_t v : bk.out_idx) rpos.push_back((int)v);
         for (int64_t v : bk.in_idx) cpos.push_back((int)v);
     }
@@ -563,6 +573,23 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
     ds.ss.blk_cols = upload(dp, blk_cols, &dp->index_bytes);
     ds.ss.blk_nrow = upload(dp, blk_nrow, &dp->index_bytes);
     ds.ss.blk_ncol = upload(dp, blk_ncol, &dp->index_bytes);
+    if (dp->s_mode == MIDBF_S_ONTHEFLY_DF) {
+        if constexpr (sizeof(R) != 4) fail(MIDBF_EINVAL, "the accurate phase applies to MIDBF_FP32 plans");
+        if (ds.s_dist) fail(MIDBF_EINVAL, "the accurate phase takes the inner-product phases, not the distance form");
+        // hi + lo of every FP64 value: hi = float(v), lo = float(v - hi)
+        auto lo_of = [](const std::vector<double>& v, std::vector<R>& hi) {
+            std::vector<R> lo(v.size());
+            for (size_t i = 0; i < v.size(); ++i) lo[i] = (R)(v[i] - (double)hi[i]);
+            return lo;
+        };
+        ds.srows.a_lo = upload(dp, lo_of(da_r, ra), &dp->factor_bytes);
+        ds.srows.u_lo = upload(dp, lo_of(du_r, ru), &dp->factor_bytes);
+        ds.srows.c_lo = upload(dp, lo_of(dc_r, rc), &dp->factor_bytes);
+        ds.scols.a_lo = upload(dp, lo_of(da_c, ca), &dp->factor_bytes);
+        ds.scols.u_lo = upload(dp, lo_of(du_c, cu), &dp->factor_bytes);
+        ds.scols.c_lo = upload(dp, lo_of(dc_c, cc), &dp->factor_bytes);
+        ds.s_df = true;
+    }
     ds.srows.a = upload(dp, ra, &dp->factor_bytes);
     ds.srows.u = upload(dp, ru, &dp->factor_bytes);
     ds.srows.c = upload(dp, rc, &dp->factor_bytes);
@@ -608,7 +635,7 @@ void make_s_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>&
 // consume: the same plan, writable; each stage's ID coefficients are released
 // from it once they are on the device.
 template <class R>
-void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out, Plan* consume) {
+void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out, Plan* consume, bool overlap) {
     int64_t in_len = pl.phase.nw;
     // overlap groups of the middle factor and the U stage after it
     std::vector<int> ck_s, ck_u;
@@ -616,7 +643,7 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out,
     for (size_t s = 0; s < pl.stages.size(); ++s)
         if (pl.stages[s].kind == KIND_S) si = (int)s;
     dp->s_stage = si;
-    const bool grouped = overlap_chunks(pl, si, kDefaultChunks, ck_s, ck_u);
+    const bool grouped = overlap && overlap_chunks(pl, si, kDefaultChunks, ck_s, ck_u);
     int nch = 0;
     if (grouped) nch = 1 + std::max(*std::max_element(ck_s.begin(), ck_s.end()), *std::max_element(ck_u.begin(), ck_u.end()));
     dp->chunks_built = grouped ? nch : 0;
@@ -907,7 +934,7 @@ std::vector<int> stage_candidates(const midbf_dplan* dp, const DevStage<R>& ds, 
             c.push_back(nr | MIDBF_CHOICE_PERSIST);
         }
     }
-    if (ds.id && !use_r && nrhs == 1 && pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap) {
+    if (ds.id && !use_r && nrhs == 1 && pattern_c1_smem<R>(ds.max_narrow, ds.max_nsub) <= kSmemCap) {
         c.push_back(MIDBF_CHOICE_COLUMN1);
         c.push_back(MIDBF_CHOICE_COLUMN1 | MIDBF_CHOICE_PERSIST);
     }
@@ -1118,11 +1145,14 @@ int midbf_dplan_create(const midbf_plan* plan, int precision, int s_mode, midbf_
 int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags, midbf_dplan** out) {
     try {
         if (!plan || !out) fail(MIDBF_EINVAL, "null argument");
-        if (flags & ~MIDBF_DPLAN_CONSUME) fail(MIDBF_EINVAL, "unknown flags");
+        if (flags & ~(MIDBF_DPLAN_CONSUME | MIDBF_DPLAN_OVERLAP)) fail(MIDBF_EINVAL, "unknown flags");
         const int base = precision & ~MIDBF_REFINE;
         if (base != MIDBF_FP64 && base != MIDBF_FP32 && base != MIDBF_BF16) fail(MIDBF_EINVAL, "unknown precision");
         if ((precision & MIDBF_REFINE) && base != MIDBF_BF16) fail(MIDBF_EINVAL, "MIDBF_REFINE applies to MIDBF_BF16");
-        if (s_mode != MIDBF_S_ONTHEFLY && s_mode != MIDBF_S_STORED) fail(MIDBF_EINVAL, "unknown middle-factor mode");
+        if (s_mode != MIDBF_S_ONTHEFLY && s_mode != MIDBF_S_STORED && s_mode != MIDBF_S_ONTHEFLY_DF)
+            fail(MIDBF_EINVAL, "unknown middle-factor mode");
+        if (s_mode == MIDBF_S_ONTHEFLY_DF && base != MIDBF_FP32)
+            fail(MIDBF_EINVAL, "the accurate phase (MIDBF_S_ONTHEFLY_DF) applies to MIDBF_FP32 plans");
         Plan& plw = *reinterpret_cast<Plan*>(plan);
         const Plan& pl = plw;
         if (pl.released) fail(MIDBF_EINVAL, "the plan's coefficients were released by an earlier consuming upload");
@@ -1141,11 +1171,17 @@ int midbf_dplan_create_ex(midbf_plan* plan, int precision, int s_mode, int flags
         if (cudaMalloc(&dp->d_status, sizeof(int)) != cudaSuccess) fail(MIDBF_ENOMEM, "cudaMalloc of the status word failed");
         CK(cudaMemset(dp->d_status, 0, sizeof(int)));
         if (consume) plw.released = true;   // from here on, whatever happens below
-        if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32, consume);
-        else make_stages<double>(dp.get(), pl, dp->st64, consume);
+        const bool overlap = (flags & MIDBF_DPLAN_OVERLAP) != 0;
+        if (dp->precision == MIDBF_FP32) make_stages<float>(dp.get(), pl, dp->st32, consume, overlap);
+        else make_stages<double>(dp.get(), pl, dp->st64, consume, overlap);
         if (dp->chunks_built > 1) {
-            // the side stream and events of the overlap (no device memory)
-            CK(cudaStreamCreateWithFlags(&dp->side, cudaStreamNonBlocking));
+            // the side stream and events of the overlap (no device memory).  The side
+            // stream gets the highest priority: its chunk k becomes ready while chunk
+            // k + 1 of the first stage is queued, and its CTAs must then take the SM slots
+            // that free up instead of waiting behind the whole next chunk.
+            int prio_lo = 0, prio_hi = 0;
+            CK(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+            CK(cudaStreamCreateWithPriority(&dp->side, cudaStreamNonBlocking, prio_hi));
             CK(cudaEventCreateWithFlags(&dp->ev_fork, cudaEventDisableTiming));
             CK(cudaEventCreateWithFlags(&dp->ev_join, cudaEventDisableTiming));
             for (int k = 0; k < dp->chunks_built; ++k) CK(cudaEventCreateWithFlags(&dp->ev_ck[k], cudaEventDisableTiming));
@@ -1381,6 +1417,7 @@ int midbf_apply_batched(int count, const midbf_dplan* const* dps, const int* adj
             if (!dp || !in[i] || !out[i] || nrhs[i] <= 0) fail(MIDBF_EINVAL, "bad instance " + std::to_string(i));
             if (dp->precision != prec) fail(MIDBF_EINVAL, "all instances must share one precision");
             if (dp->device != dps[0]->device) fail(MIDBF_EINVAL, "all instances must live on one device");
+            if (dp->s_mode == MIDBF_S_ONTHEFLY_DF) fail(MIDBF_EINVAL, "the batched apply does not take accurate-phase plans");
             const int64_t nin = adjoint[i] ? dp->nx : dp->nw, nout = adjoint[i] ? dp->nw : dp->nx;
             if (ldin[i] < nin || ldout[i] < nout) fail(MIDBF_EINVAL, "leading dimension too small for instance " + std::to_string(i));
         }

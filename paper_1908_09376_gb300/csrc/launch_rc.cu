@@ -80,7 +80,7 @@ void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
               bool persist) {
     if (ds.n_items_c == 0) return;
     if (nrhs == 1 && (force == 0 || force == MIDBF_CHOICE_COLUMN1)) {
-        const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
+        const size_t sm = pattern_c1_smem<R>(ds.max_narrow, ds.max_nsub);
         if (sm <= kSmemCap) {
             const int n = ds.n_items_c1;
             if (persist) {

@@ -68,9 +68,53 @@ void launch_s_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, 
     }
 }
 
+// The accurate phase (FP32, one RHS per pass, 64-row items).
+template <bool CJ, int PQ>
+void launch_s_df_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, cudaStream_t s,
+                   bool persist) {
+    SStage<float> st = ds.ss;
+    const size_t sm = s_fly_df_smem(st.P, st.Q, 2);
+    st.items = !CJ ? ds.items_rows : ds.items_cols;
+    const int n = !CJ ? ds.n_items_rows : ds.n_items_cols;
+    if (n == 0) return;
+    const SSide<float>& rside = !CJ ? ds.srows : ds.scols;
+    const SSide<float>& cside = !CJ ? ds.scols : ds.srows;
+    if (persist) {
+        auto kf = k_s_fly_df_p<2, CJ, PQ>;
+        set_smem(kf, sm);
+        kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(st, rside, cside, !CJ ? 1 : 0,
+                                                                                       src, dst, nrhs, n);
+    } else {
+        auto kf = k_s_fly_df<2, CJ, PQ>;
+        set_smem(kf, sm);
+        kf<<<n, kThreads, sm, s>>>(st, rside, cside, !CJ ? 1 : 0, src, dst, nrhs);
+    }
+}
+
+template <bool CJ>
+void launch_s_df(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, cudaStream_t s,
+                 bool persist) {
+    switch (phase_shape_code(ds.ss.P, ds.ss.Q)) {
+        case 1: launch_s_df_t<CJ, 1>(ds, src, dst, nrhs, s, persist); break;
+        case 2: launch_s_df_t<CJ, 2>(ds, src, dst, nrhs, s, persist); break;
+        case 3: launch_s_df_t<CJ, 3>(ds, src, dst, nrhs, s, persist); break;
+        case 4: launch_s_df_t<CJ, 4>(ds, src, dst, nrhs, s, persist); break;
+        case 5: launch_s_df_t<CJ, 5>(ds, src, dst, nrhs, s, persist); break;
+        default: launch_s_df_t<CJ, 0>(ds, src, dst, nrhs, s, persist);
+    }
+}
+
 template <class R>
 void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s, int force,
               bool persist) {
+    if constexpr (sizeof(R) == 4) {
+        if (ds.s_df) {
+            if (adjoint) launch_s_df<true>(ds, src, dst, nrhs, s, persist);
+            else launch_s_df<false>(ds, src, dst, nrhs, s, persist);
+            CK(cudaGetLastError());
+            return;
+        }
+    }
     const int nr = forced_or_pick<R>(force, nrhs, [&](int q) { return s_fly_smem<R>(ds.ss.P, ds.ss.Q, q <= 4 && sizeof(R) == 4 ? 4 : 2, q); });
     if (adjoint) launch_s_nr<R, true>(ds, src, dst, nrhs, nr, s, persist);
     else launch_s_nr<R, false>(ds, src, dst, nrhs, nr, s, persist);

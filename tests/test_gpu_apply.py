@@ -191,3 +191,45 @@ def test_autograd_finite_differences():
             fd = (loss(f + h * d) - loss(f - h * d)) / (2 * h)
         dd = torch.real(torch.vdot(grad, d))
         assert abs(fd.item() - dd.item()) <= 1e-9 * max(1.0, abs(dd.item())), i
+
+
+# The accurate phase (MIDBF_S_ONTHEFLY_DF): every middle-factor entry's phase
+# in double-FP32 arithmetic.  What remains of the FP32 error is the storage of
+# T and the vectors in FP32 (6e-8 relative), FP32 accumulation over ~10
+# stages, and the SFU sine/cosine (absolute error ~4e-7): bound 2e-6, ten
+# times tighter than the FP32 bound, and the result must beat the ordinary
+# FP32 phase on the same factors.
+DF_TOL = 2e-6
+
+
+@pytest.mark.parametrize("case", ["fio2d_n32_L3", "fio2d_n64_L3", "jump_n32_L2", "fio3d_n8_L2", "lowrank_n32_L3",
+                                  "dot_n16_L2"])
+def test_accurate_phase_matches_oracle(case):
+    fac, plan, mats = oracle_case(case)
+    dp = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY_DF)
+    dq = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY)
+    for nrhs in (1, 3):
+        f = synth.complex_gaussian(fac.nw, nrhs, 30 + nrhs)
+        y = synth.complex_gaussian(fac.nx, nrhs, 40 + nrhs)
+        F = torch.from_numpy(f.T.copy()).to("cuda", torch.complex64)
+        Y = torch.from_numpy(y.T.copy()).to("cuda", torch.complex64)
+        g = dp.apply(F).cpu().numpy().T
+        a = dp.apply(Y, adjoint=True).cpu().numpy().T
+        g_ref = midbf.apply(fac, f, mats)
+        a_ref = midbf.apply_adjoint(fac, y, mats)
+        _check(g, g_ref, DF_TOL, f"{case} accurate forward nrhs={nrhs}")
+        _check(a, a_ref, DF_TOL, f"{case} accurate adjoint nrhs={nrhs}")
+        gq = dq.apply(F).cpu().numpy().T
+        assert direct.rel_l2(g, g_ref) <= direct.rel_l2(gq, g_ref) * 1.01 + 1e-7, case
+
+
+def test_accurate_phase_rejections():
+    fac, plan, _ = oracle_case("fio2d_n32_L3")
+    for prec in (mb.FP64, mb.BF16, mb.BF16 | mb.REFINE):
+        with pytest.raises(mb.MidbfError) as e:
+            mb.DevicePlan(plan, prec, mb.S_ONTHEFLY_DF)
+        assert e.value.code == mb.EINVAL
+    dp = mb.DevicePlan(plan, mb.FP32, mb.S_ONTHEFLY_DF)
+    x = torch.zeros(fac.nw, dtype=torch.complex64, device="cuda")
+    with pytest.raises(mb.MidbfError):
+        mb.apply_batched([dp], [x], [0])

@@ -185,3 +185,26 @@ def test_recovered_phase_paper_discretization():
         g = dp.apply(torch.from_numpy(f).to("cuda", dt)).cpu().numpy()
         e = direct.rel_l2(g[rows], ref)
         assert e < tol, (prec, e)
+
+
+def test_fullsize_accurate_phase(plan):
+    """The mixed form with the accurate phase (double-FP32 middle-factor
+    phases, MIDBF_S_ONTHEFLY_DF) at the benchmark's size: within 2e-6 of the
+    FP64 plain form of the same factors (the ordinary FP32 phase is ~1e-5
+    there: its rounding grows with the phase's magnitude, ~35 cycles at
+    n = 256), and within 2e-6 of the oracle's direct sums on sampled rows
+    (the factors themselves are accurate to ~6e-7)."""
+    pl, oph = plan
+    N = N_GRID ** 2
+    ddf = mb.DevicePlan(pl, mb.FP32, mb.S_ONTHEFLY_DF)
+    d64 = mb.DevicePlan(pl, mb.FP64, mb.S_STORED)
+    f = synth.complex_gaussian(N, 1, 0)[:, 0]
+    for adj in (False, True):
+        gdf = ddf.apply(torch.from_numpy(f).to("cuda", torch.complex64), adjoint=adj).to(torch.complex128)
+        g64 = d64.apply(torch.from_numpy(f).to("cuda", torch.complex128), adjoint=adj)
+        rel = (torch.linalg.vector_norm(gdf - g64) / torch.linalg.vector_norm(g64)).item()
+        assert rel < 2e-6, (adj, rel)
+    g = ddf.apply(torch.from_numpy(f).to("cuda", torch.complex64)).cpu().numpy()
+    rows = synth.sample_rows(N, 256, 3)
+    e = direct.rel_l2(g[rows], direct.direct_sum(oph, f, rows=rows))
+    assert e < 2e-6, e

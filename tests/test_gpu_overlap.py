@@ -8,6 +8,8 @@ accumulation order are the same as with the overlap off, so every result must
 be the same bit for bit: forward and adjoint, FP32 and FP64, one RHS and a
 few, through midbf_apply, a recorded graph and midbf_apply_noalloc; and the
 oracle's apply of the same factors bounds the result as for every apply.
+Plans get the overlap only when asked (MIDBF_DPLAN_OVERLAP); without it they
+have no chunks.
 """
 import numpy as np
 import pytest
@@ -36,7 +38,7 @@ def _case(n):
 @pytest.mark.parametrize("prec,s_mode", [(mb.FP32, mb.S_ONTHEFLY), (mb.FP64, mb.S_ONTHEFLY), (mb.FP32, mb.S_STORED)])
 def test_overlap_gives_the_same_bits(prec, s_mode):
     fac, plan, mats = _case(64)
-    dp = mb.DevicePlan(plan, prec, s_mode)
+    dp = mb.DevicePlan(plan, prec, s_mode, overlap=True)
     assert dp.overlap() > 1                       # four groups of four blocks at n = 64
     dt = dp.dtype()
     tol = 1e-12 if prec == mb.FP64 else 2e-5
@@ -61,7 +63,7 @@ def test_overlap_gives_the_same_bits(prec, s_mode):
 
 def test_overlap_in_a_graph_and_without_allocation():
     fac, plan, _ = _case(64)
-    dp = mb.DevicePlan(plan, mb.FP32)
+    dp = mb.DevicePlan(plan, mb.FP32, overlap=True)
     assert dp.overlap() > 1
     N = fac.nw
     f = torch.zeros(N, dtype=torch.complex64, device="cuda")
@@ -89,3 +91,11 @@ def test_overlap_in_a_graph_and_without_allocation():
     mb.check(mb.midbf_apply_noalloc(dp.h, 0, F.data_ptr(), N, y.data_ptr(), N, 1, cs), "midbf_apply_noalloc")
     torch.cuda.synchronize()
     assert torch.equal(y, g_ref)
+
+
+def test_plans_have_no_overlap_unless_asked():
+    fac, plan, _ = _case(64)
+    assert mb.DevicePlan(plan, mb.FP32).overlap() == 0
+    dp = mb.DevicePlan(plan, mb.FP32, overlap=True)
+    assert dp.overlap() == 4
+    assert dp.workspace_bytes(1) > mb.DevicePlan(plan, mb.FP32).workspace_bytes(1)   # the third vector
