@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--tune", default=None, choices=["on", "off"],
                     help="run the autotuner for the RHS count before timing (default: on for fio2d_jump)")
     ap.add_argument("--graph", default=None, choices=["on", "off"],
-                    help="time the step as one CUDA-graph replay (default: on for fio2d_jump)")
+                    help="time the step as one CUDA-graph replay (default: on for fio2d_jump and the one-RHS fio2d step)")
     ap.add_argument("--store", default=None, choices=["fp64", "fp32"],
                     help="host storage of the IDs' coefficients (default fp64; fp32 for fio2d_jump, whose "
                          "n = 1024 plan does not fit host memory in FP64)")
@@ -178,9 +178,20 @@ def pick_workload(args):
     store = args.store if args.store is not None else ("fp32" if args.workload == "fio2d_jump" else "fp64")
     jump = args.workload == "fio2d_jump"
     tune = (args.tune or ("on" if jump else "off")) == "on"
-    graph = (args.graph or ("on" if jump else "off")) == "on"
+    # the step as one CUDA-graph replay: the default for the one-RHS headline (its 14
+    # launches cost ~2% of the step when issued one by one) and for the n = 1024 plan
+    graph = (args.graph or ("on" if jump or (args.workload == "fio2d" and nrhs == 1) else "off")) == "on"
     return w, nrhs, mode, build, store, tune, graph
 
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture of the kernel as it stands, keyed by (workload, direction, stage index in
+# launch order, stage kind); summaries under profiles/.
+NCU_TRAFFIC = {
+    ("fio2d_n256", "adj", 4, 0): (1.6225e9, "profiles/k_pattern_c1_fio2d_n256_full.md"),
+    ("fio2d_n256", "fwd", 2, 0): (1.6241e9, "profiles/k_pattern_fio2d_n256_full.md"),
+    ("fio2d_n256", "fwd", 3, 1): (0.0169e9, "profiles/k_s_fly_fio2d_n256_full.md"),
+}
 
 # Table 2 of the paper: T_app (s) for Example 1 at n = 16 ... 4096 with r = 10, k = 30.
 TABLE2_T_APP = {16: 2.81e-4, 64: 4.43e-3, 256: 4.00e-2, 1024: 6.86e-1, 4096: 1.64e1}
@@ -533,6 +544,75 @@ def main_batched(args, ws, rank, dev, pg):
         print(json.dumps(out), flush=True)
 
 
+def fio3d_leg(args, dev, stream, flush):
+    """The 3D FIO workload (d = 3, N = 32,768 random points, xi in [-16, 16)^3,
+    256 RHS, BF16 tensor cores with the refinement products) measured beside
+    the headline: forward + adjoint step time, the tensor-pipe fractions of the
+    middle factor, and rel-L2 against FP64 direct sums on 512 sampled rows and
+    columns."""
+    import torch
+    import paper_1908_09376_gb300 as mb
+    wl = synth.WORKLOADS["fio3d_n32"]
+    X, W, bx, bw = wl.points()
+    ph = mb.Phase.closed_form(wl.phase, X, W)
+    t0 = time.perf_counter()
+    plan = mb.Plan.build(ph, tol=wl.tol, n0=wl.n0, boxX=bx, boxW=bw, nthreads=args.threads, t=wl.t, device_ids=1)
+    t_build = time.perf_counter() - t0
+    dp = mb.DevicePlan(plan, mb.BF16 | mb.REFINE, mb.S_ONTHEFLY, consume=True)
+    del plan
+    R = wl.nrhs
+    sinfo = dp.stage_info()
+    ns = len(sinfo)
+    f_host = synth.complex_gaussian(wl.nw, R, wl.f_seed)
+    F = torch.from_numpy(f_host.T.copy()).to(dev, torch.complex64)
+    G = torch.empty((R, wl.nx), dtype=torch.complex64, device=dev)
+    H = torch.empty((R, wl.nw), dtype=torch.complex64, device=dev)
+    wsb = torch.empty(dp.workspace_bytes(R), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        dp.apply(F, out=G, workspace=wsb)
+        dp.apply(G, adjoint=True, out=H, workspace=wsb)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    k = 3
+    for _ in range(k):
+        flush.zero_()
+        e0.record(stream)
+        dp.apply(F, out=G, workspace=wsb)
+        dp.apply(G, adjoint=True, out=H, workspace=wsb)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    ms = tot / k
+    dp.profile(True)
+    s_rows = []
+    for adj in (False, True):
+        flush.zero_()
+        dp.apply(G if adj else F, adjoint=adj, out=H if adj else G, workspace=wsb)
+        for q, (kind, sms, _) in enumerate(dp.stage_times()):
+            if kind == 1:
+                sidx = ns - 1 - q if adj else q
+                alg = 8.0 * sinfo[sidx][1] * R / (sms * 1e-3) / 1e12
+                s_rows.append({"dir": "adj" if adj else "fwd", "ms": round(sms, 4), "TFLOPs_algorithmic": round(alg, 1),
+                               "TFLOPs_issued": round(3 * alg, 1), "issued_frac": round(3 * alg / PEAK_BF16, 4)})
+    dp.profile(False)
+    dp.apply(F, out=G, workspace=wsb)
+    dp.apply(G, adjoint=True, out=H, workspace=wsb)
+    torch.cuda.synchronize()
+    rows = synth.sample_rows(wl.nx, wl.sample_rows, wl.sample_seed)
+    cols = synth.sample_rows(wl.nw, wl.sample_rows, wl.sample_seed + 1)
+    Gn, Hn = G.cpu().numpy(), H.cpu().numpy()
+    e_f, e_a = sampled_direct_error(ph, f_host.T, Gn, Gn, Hn, rows, cols)
+    out = {"workload": wl.name, "N": wl.N, "nrhs": R, "mode": "bf16r", "ms_per_step": round(ms, 4),
+           "value": (wl.nx + wl.nw) * R / (ms * 1e-3), "unit": "points*RHS/s", "build_s": round(t_build, 1),
+           "s_stage": s_rows, "peak_TFLOPs": PEAK_BF16, "peak_source": PEAK_BF16_SOURCE,
+           "rel_l2_direct_sampled": {"forward": e_f, "adjoint": e_a, "rows": wl.sample_rows},
+           "status": dp.status(), "l2": "flushed (512 MB write) between timed steps"}
+    del dp, wsb, F, G, H
+    torch.cuda.empty_cache()
+    return out
+
+
 def main_sweep(args, ws, rank, dev, pg):
     """Fig. 8's scaling in N: the FIO2D family (Example 1's phase on the n x n
     grid, ID tolerance 1e-6, n0 = 64) at each n of --sweep, one RHS, FP32,
@@ -826,7 +906,7 @@ def main():
     # reciprocal square root; the SFU completes 16 operations per clock per SM
     sfu_ops = 3 if wl.phase in (synth.PHASE_FIO2D, synth.PHASE_FIO3D, synth.PHASE_FIO2D_JUMP,
                                 synth.PHASE_DISTANCE) and not wl.recovered else 2
-    fma_rate, sfu_rate = mb.pipe_rates(stream)      # measured on this GPU (midbf_pipe_rates)
+    fma_rate, sfu_rate, dfma_rate = mb.pipe_rates(stream)   # measured on this GPU (midbf_pipe_rates)
     sfu_peak = sfu_rate / sfu_ops / 1e9             # G entries/s
     s_entries_of = {q_: sinfo[q_][1] for q_ in range(ns) if sinfo[q_][0] == 1}
 
@@ -867,6 +947,20 @@ def main():
                     "whole_step_GBps": round(all_bytes / (ms_per_step * 1e-3) / 1e9, 1),
                     "whole_step_frac": round(all_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4)}
 
+    def fill_traffic(rf, key, alg_bytes):
+        if rf is None or key not in NCU_TRAFFIC or R1 != 1 or mode_name != "fp32":
+            return
+        t, src = NCU_TRAFFIC[key]
+        rf["traffic"] = t
+        rf["traffic_over_algorithmic"] = round(t / alg_bytes, 4)
+        rf["traffic_source"] = src + " (ncu, one launch)"
+
+    fill_traffic(roofline, (wl.name, direction, q, kind), by)
+    if roofline_hbm is not None:
+        k_ = roofline_hbm["kernel"].split()
+        dq = (k_[0], int(k_[2]), "VSU".index(k_[3].strip("()")))
+        by_ = next(kk[3] for kk in stage_ms if (kk[0], kk[1], kk[2]) == dq)
+        fill_traffic(roofline_hbm, (wl.name,) + dq, by_)
     log("timed")
     # accuracy of this run's outputs against FP64 direct sums on sampled rows / columns
     acc = None
@@ -959,8 +1053,16 @@ def main():
         torch.cuda.synchronize()
         rel_fwd = (torch.linalg.vector_norm(g.to(torch.complex128) - g64) / torch.linalg.vector_norm(g64)).item()
         rel_adj = (torch.linalg.vector_norm(h.to(torch.complex128) - h64) / torch.linalg.vector_norm(h64)).item()
+        # a complex multiply-add is 4 FP64 FMAs; every stored T and S entry once per direction
+        fma64 = 2 * 4.0 * (st["t_entries"] + st["s_entries"])
         extras["plain_fp64"] = {"value": 2 * N / (ms64 * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(ms64, 4),
-                                "s_mode": "stored", "bound": "alu(fp64)"}
+                                "s_mode": "stored", "bound": "alu(fp64)",
+                                "roofline": {"bound": "alu", "achieved": round(fma64 / (ms64 * 1e-3) / 1e9, 1),
+                                             "peak": round(dfma_rate / 1e9, 1), "unit": "G FP64 FMA/s",
+                                             "frac": round(fma64 / (ms64 * 1e-3) / dfma_rate, 4),
+                                             "peak_source": "measured FP64 FMA rate (midbf_pipe_rates)",
+                                             "work": "4 FP64 FMAs per complex multiply-add of every T and S entry, "
+                                                     "forward and adjoint"}}
         extras["speedup_mixed_vs_plain"] = round(ms64 / ms_per_step, 3)
         extras["rel_l2_fp32_vs_fp64"] = {"forward": rel_fwd, "adjoint": rel_adj}
         # the mixed form with the accurate phase (double-FP32 middle-factor phases)
@@ -1078,6 +1180,9 @@ def main():
                 "rel_l2_vs_fp32": rel_tc, "status": dptc.status()}
             del wsR, F, Gt, Ht
         del G, H, Gref, dptc
+        torch.cuda.empty_cache()
+        # the 3D FIO workload with 256 RHS on the tensor cores, beside the headline
+        extras["fio3d_n32_256rhs_bf16r"] = fio3d_leg(args, dev, stream, flush)
 
     # end to end through the host-buffer entry point (pinned host memory)
     fh = torch.from_numpy(f_host.T.astype(np.complex64).copy()).pin_memory()
@@ -1131,7 +1236,8 @@ def main():
            "roofline": roofline, "roofline_hbm": roofline_hbm, "stages": stage_rows, "rel_l2_direct_sampled": acc,
            "overlap": {"chunks": overlap_chunks, "without": no_overlap,
                        "note": "middle factor and its U stage run chunk by chunk on two streams (midbf_dplan_set_overlap)"},
-           "pipe_rates": {"fma_per_s": fma_rate, "sfu_per_s": sfu_rate, "source": "midbf_pipe_rates, measured"},
+           "pipe_rates": {"fma_per_s": fma_rate, "sfu_per_s": sfu_rate, "fp64_fma_per_s": dfma_rate,
+                          "source": "midbf_pipe_rates, measured"},
            "clocks": clk, "e2e": e2e,
            "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
     out.update(extras)

@@ -431,6 +431,11 @@ void midbf_graph_destroy(midbf_graph* graph);
 #define MIDBF_CHOICE_COLUMN1 32
 #define MIDBF_CHOICE_PERSIST 256
 #define MIDBF_CHOICE_TENSOR 1024
+#define MIDBF_CHOICE_NARROW 64   /* one RHS, every rank <= 64: a warp per ID (rows) or
+                                    a lane per column (columns); the default for
+                                    stages whose ranks are all <= 48 (and, for
+                                    the rows, whose IDs have <= 128 redundant
+                                    columns) */
 int midbf_autotune(midbf_dplan* dp, int nrhs, void* stream);
 int midbf_set_choice(midbf_dplan* dp, int nrhs, int stage, int adjoint, int choice);
 int midbf_get_choice(const midbf_dplan* dp, int nrhs, int stage, int adjoint, int* choice);
@@ -464,12 +469,13 @@ int midbf_stage_info(const midbf_dplan* dp, int max_stages, int* kinds, int64_t*
 
 /* Measured arithmetic rates of the current device (for rooflines of the
  * kernels bound by arithmetic): FP32 fused multiply-adds per second (eight
- * independent chains per thread) and SFU operations per second (chains of
- * rsqrt.approx), both over every SM, best of three timed launches on stream.
+ * independent chains per thread), SFU operations per second (chains of
+ * rsqrt.approx) and, when dfma_per_s is not NULL, FP64 fused multiply-adds
+ * per second; all over every SM, best of three timed launches on stream.
  * Allocates a small device buffer and synchronizes.  The paper has no
  * counterpart: this is measurement support.  Errors: MIDBF_EINVAL,
  * MIDBF_ECUDA. */
-int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per_s);
+int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per_s, double* dfma_per_s);
 
 /* midbf_apply_noalloc: midbf_apply for callers that cannot allocate device
  * memory when they apply the operator - for example a service whose GPU

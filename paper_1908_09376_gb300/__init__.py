@@ -23,7 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 # ---- constants (include/midbf.h) ------------------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ECALLBACK, ERANK, ERECOVERY, ETIMEOUT, EINTERNAL, EFORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
-CHOICE_DEFAULT, CHOICE_COLUMN1, CHOICE_PERSIST, CHOICE_TENSOR = 0, 32, 256, 1024
+CHOICE_DEFAULT, CHOICE_COLUMN1, CHOICE_PERSIST, CHOICE_TENSOR, CHOICE_NARROW = 0, 32, 256, 1024, 64
 PHASE_FIO2D, PHASE_FIO3D, PHASE_FIO2D_JUMP, PHASE_DOT, PHASE_ZERO, PHASE_SEPARABLE, PHASE_LOWRANK = 1, 2, 3, 4, 5, 6, 7
 PHASE_DISTANCE = 8
 FP64, FP32, BF16, REFINE = 0, 1, 2, 16
@@ -136,16 +136,16 @@ midbf_apply_batched = _sig("midbf_apply_batched", C.c_int,
 midbf_apply_noalloc = _sig("midbf_apply_noalloc", C.c_int,
                            [_vp, C.c_int, _vp, C.c_int64, _vp, C.c_int64, C.c_int, _vp])
 midbf_noalloc_scratch_bytes = _sig("midbf_noalloc_scratch_bytes", C.c_size_t, [])
-midbf_pipe_rates = _sig("midbf_pipe_rates", C.c_int, [_vp, _dblp, _dblp])
+midbf_pipe_rates = _sig("midbf_pipe_rates", C.c_int, [_vp, _dblp, _dblp, _dblp])
 
 
 def pipe_rates(stream=None):
-    """(FP32 FMAs per second, SFU operations per second) measured on the current device."""
+    """(FP32 FMAs/s, SFU operations/s, FP64 FMAs/s) measured on the current device."""
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
-    a, b = C.c_double(), C.c_double()
-    check(midbf_pipe_rates(s.cuda_stream, C.byref(a), C.byref(b)), "midbf_pipe_rates")
-    return a.value, b.value
+    a, b, c = C.c_double(), C.c_double(), C.c_double()
+    check(midbf_pipe_rates(s.cuda_stream, C.byref(a), C.byref(b), C.byref(c)), "midbf_pipe_rates")
+    return a.value, b.value, c.value
 
 EXPORTED = [n for n in dir() if n.startswith("midbf_") and callable(globals()[n])
             and not isinstance(globals()[n], type)]

@@ -69,6 +69,7 @@ struct DevStage : DevStageBase {
     IdStage<R> ids{};
     IdStage<R> ids1{};   // same data, items for the one-RHS pattern-C kernel
     int n_items_r = 0, n_items_c = 0, n_items_c1 = 0, rt = 1;
+    int n_subs = 0, max_k = 0;          // interpolative decompositions of the stage, their largest rank
     int max_nred = 0, max_narrow = 0, max_nsub = 1;
     // on-the-fly S
     SStage<R> ss{};
@@ -195,21 +196,39 @@ int grid_for(const void* kernel, size_t smem, int nitems, bool persist);
 int sm_count();
 void launch_wait_selftest(int* status, int ctas, cudaStream_t s);
 
+constexpr int kNarrowK = 48;      // one RHS: the narrow-ID kernels for stages whose ranks are all <= this
+constexpr int kNarrowRed = 128;   // and (row pattern) whose IDs have at most this many redundant columns
 constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
 constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
 
 
 // SIMT RHS tile named by a choice (0: none).
 inline int choice_tile(int choice) {
-    const int base = choice == MIDBF_CHOICE_TENSOR ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
+    const int base = (choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW) ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
     return base >= 1 && base <= 16 ? base : 0;
 }
 
 inline bool valid_choice(int choice) {
-    if (choice == MIDBF_CHOICE_TENSOR) return true;
+    if (choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW) return true;
     const int base = choice & ~MIDBF_CHOICE_PERSIST;
     return base == MIDBF_CHOICE_DEFAULT || base == MIDBF_CHOICE_COLUMN1 || base == 1 || base == 2 || base == 4 ||
            base == 8 || base == 16;
+}
+
+// Whether a one-RHS ID-stage launch takes the narrow-ID kernels: asked for
+// (MIDBF_CHOICE_NARROW), or by default when every rank is at most kNarrowK
+// and, for the row pattern (a warp walks all the redundant columns of its ID
+// alone), every ID has at most kNarrowRed redundant columns; never for a
+// stage prepared for the overlap (those launch chunks of items).  Measured
+// on one GB300: the paper-grid plan of Example 1 (ranks ~11, ~33 redundant
+// columns) runs its stages in about half the time, while Example 2's leaf
+// IDs (rank 44, 468 redundant columns) ran 5x slower in the row pattern,
+// with too few warps for the serial column walk.
+template <class R>
+inline bool use_narrow(const DevStage<R>& ds, int nrhs, int choice, bool row_pattern) {
+    if (nrhs != 1 || !ds.id || ds.nchunks != 0 || ds.max_k > 64) return false;
+    if (choice == MIDBF_CHOICE_NARROW) return true;
+    return choice == MIDBF_CHOICE_DEFAULT && ds.max_k <= kNarrowK && (!row_pattern || ds.max_nred <= kNarrowRed);
 }
 
 // Internal vectors of the workspace: the two ping-pong vectors, and a third
@@ -241,6 +260,10 @@ void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
 template <class R>
 void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force = 0,
               bool persist = false);
+template <class R>
+void launch_r_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s);
+template <class R>
+void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s);
 template <class R>
 void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s,
               int force = 0, bool persist = false);

@@ -362,6 +362,8 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     }
     ds.id = true;
     ds.rt = rt;
+    ds.n_subs = (int)subs.size();
+    ds.max_k = maxk;
     ds.n_items_r = (int)items_r.size();
     ds.n_items_c = (int)items_c.size();
     ds.max_nred = (int)max_nred;
@@ -772,14 +774,19 @@ void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, Ve
             return;
         }
     }
-    const bool persist = choice != MIDBF_CHOICE_TENSOR && (choice & MIDBF_CHOICE_PERSIST) != 0;
+    const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
+    // pattern R computes narrow from wide; pattern C wide from narrow.
+    const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
+    const bool narrow = use_narrow(ds, nrhs, choice, use_r);
+    const bool persist = !narrow && choice != MIDBF_CHOICE_TENSOR && (choice & MIDBF_CHOICE_PERSIST) != 0;
     const int tile = choice_tile(choice);
-    const bool col1 = choice != MIDBF_CHOICE_TENSOR && (choice & ~MIDBF_CHOICE_PERSIST) == MIDBF_CHOICE_COLUMN1;
+    const bool col1 = !narrow && choice != MIDBF_CHOICE_TENSOR &&
+                      (choice & ~MIDBF_CHOICE_PERSIST) == MIDBF_CHOICE_COLUMN1;
     if (ds.id) {
-        const bool wide_is_fwd_input = ds.kind != KIND_U;  // V and stored S
-        // pattern R computes narrow from wide; pattern C wide from narrow.
-        const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
-        if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
+        if (narrow) {
+            if (use_r) launch_r_narrow<R>(ds, src, dst, adjoint, s);
+            else launch_c_narrow<R>(ds, src, dst, adjoint, s);
+        } else if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
         else launch_c<R>(ds, src, dst, nrhs, adjoint, s, col1 ? MIDBF_CHOICE_COLUMN1 : tile, persist);
     } else {
         launch_s<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
@@ -938,6 +945,9 @@ std::vector<int> stage_candidates(const midbf_dplan* dp, const DevStage<R>& ds, 
         c.push_back(MIDBF_CHOICE_COLUMN1);
         c.push_back(MIDBF_CHOICE_COLUMN1 | MIDBF_CHOICE_PERSIST);
     }
+    if (ds.id && nrhs == 1 && ds.nchunks == 0 && ds.max_k <= 64 &&
+        (use_r || pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap))
+        c.push_back(MIDBF_CHOICE_NARROW);
     if (sizeof(R) == 4 && (ds.id ? ds.tc : dp->tc_mode != 0)) c.push_back(MIDBF_CHOICE_TENSOR);
     return c;
 }

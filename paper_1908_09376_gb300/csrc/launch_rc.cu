@@ -102,6 +102,37 @@ void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
     CK(cudaGetLastError());
 }
 
+// One RHS, narrow IDs (every rank <= 64): a warp per sub-block for pattern R,
+// a lane per column for pattern C.
+template <class R>
+void launch_r_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s) {
+    if (ds.n_subs == 0) return;
+    const int grid = (ds.n_subs + kWarps - 1) / kWarps;
+    if (ds.max_k <= 32) {
+        if (conj) k_pattern_r1n<R, 1, true><<<grid, kThreads, 0, s>>>(ds.ids, src, dst, ds.n_subs);
+        else k_pattern_r1n<R, 1, false><<<grid, kThreads, 0, s>>>(ds.ids, src, dst, ds.n_subs);
+    } else {
+        if (conj) k_pattern_r1n<R, 2, true><<<grid, kThreads, 0, s>>>(ds.ids, src, dst, ds.n_subs);
+        else k_pattern_r1n<R, 2, false><<<grid, kThreads, 0, s>>>(ds.ids, src, dst, ds.n_subs);
+    }
+    CK(cudaGetLastError());
+}
+
+template <class R>
+void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s) {
+    if (ds.n_items_c1 == 0) return;
+    const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
+    auto kf = conj ? k_pattern_c1n<R, true> : k_pattern_c1n<R, false>;
+    set_smem(kf, sm);
+    kf<<<ds.n_items_c1, kThreads, sm, s>>>(ds.ids1, src, dst);
+    CK(cudaGetLastError());
+}
+
+template void launch_r_narrow<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, cudaStream_t);
+template void launch_r_narrow<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, bool, cudaStream_t);
+template void launch_c_narrow<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, cudaStream_t);
+template void launch_c_narrow<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, bool, cudaStream_t);
+
 template void launch_r<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
 template void launch_r<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
 template void launch_c<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);

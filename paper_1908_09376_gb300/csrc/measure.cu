@@ -2,8 +2,9 @@
 // kernels bound by arithmetic rather than memory (the middle factor made on
 // the fly: one sine, one cosine and, for the FIO phases, one reciprocal
 // square root per entry on the SFU, and about twenty FP32 FMA-pipe
-// operations).  Two throughput loops, timed with CUDA events:
-//   - FP32 FMA: eight independent fused multiply-add chains per thread;
+// operations; the plain FP64 form, bound by FP64 FMAs).  Throughput loops,
+// timed with CUDA events:
+//   - FP32 and FP64 FMA: eight independent fused multiply-add chains per thread;
 //   - SFU: eight independent chains of rsqrt.approx per thread (one SFU
 //     operation each; the add that keeps the chains finite runs on the FMA
 //     pipe, which has four times the rate).
@@ -35,6 +36,19 @@ __global__ void __launch_bounds__(256) k_fma_rate(float* out, int iters, float b
     if (s == 12345.0f) out[blockIdx.x] = s;   // keeps the chains alive; never true for these inputs
 }
 
+__global__ void __launch_bounds__(256) k_dfma_rate(double* out, int iters, double b, double c) {
+    double a[kChains];
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) a[q] = (double)(threadIdx.x + q) * 1e-3;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int q = 0; q < kChains; ++q) a[q] = fma(a[q], b, c);
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < kChains; ++q) s += a[q];
+    if (s == 12345.0) out[blockIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(256) k_sfu_rate(float* out, int iters, float c) {
     float a[kChains];
 #pragma unroll
@@ -54,7 +68,7 @@ __global__ void __launch_bounds__(256) k_sfu_rate(float* out, int iters, float c
 
 }  // namespace
 
-extern "C" int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per_s) {
+extern "C" int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per_s, double* dfma_per_s) {
     float* out = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc = MIDBF_OK;
@@ -65,7 +79,7 @@ extern "C" int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per
         MCK(cudaGetDevice(&dev));
         MCK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         const int grid = 8 * nsm, threads = 256;
-        MCK(cudaMalloc(&out, grid * sizeof(float)));
+        MCK(cudaMalloc(&out, grid * sizeof(double)));
         MCK(cudaEventCreate(&e0));
         MCK(cudaEventCreate(&e1));
         auto time = [&](auto launch) {
@@ -87,9 +101,14 @@ extern "C" int midbf_pipe_rates(void* stream, double* fma_per_s, double* sfu_per
         MCK(cudaGetLastError());
         const double t_sfu = time([&] { k_sfu_rate<<<grid, threads, 0, s>>>(out, it_sfu, 1.0f); });
         MCK(cudaGetLastError());
+        const int it_dfma = 256;
+        const double t_dfma =
+            time([&] { k_dfma_rate<<<grid, threads, 0, s>>>(reinterpret_cast<double*>(out), it_dfma, 0.999, 1e-3); });
+        MCK(cudaGetLastError());
         const double n = (double)grid * threads * kChains;
         *fma_per_s = n * it_fma / t_fma;
         *sfu_per_s = n * it_sfu / t_sfu;
+        if (dfma_per_s) *dfma_per_s = n * it_dfma / t_dfma;
     } catch (const midbf::Error& e) {
         midbf::set_last_error(e.what());
         rc = e.code;

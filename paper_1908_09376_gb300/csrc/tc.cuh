@@ -702,3 +702,4 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_blk_tc(TcStage st, const __nv
 }
 
 }  // namespace midbf_dev
+

@@ -47,7 +47,10 @@ def test_workload_defaults():
     class A:
         workload, n, nrhs, mode, build, store, tune, graph = "fio2d", None, None, None, None, None, None, None
     w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
-    assert (w.n, nrhs, mode, build, store, tune, graph) == (256, 1, "fp32", "host", "fp64", False, False)
+    assert (w.n, nrhs, mode, build, store, tune, graph) == (256, 1, "fp32", "host", "fp64", False, True)
+    A.nrhs = 64
+    assert bench.pick_workload(A)[6] is False      # the graph default is for the one-RHS step only
+    A.nrhs = None
     A.workload = "fio3d_n32"
     w, nrhs, mode, *_ = bench.pick_workload(A)
     assert (w.d, w.N, nrhs, mode) == (3, 32768, 256, "bf16r")
@@ -60,6 +63,13 @@ def test_workload_defaults():
     A.workload = "helmholtz"
     w, nrhs, mode, *_ = bench.pick_workload(A)
     assert (w.nx, w.nw, nrhs, mode, w.t, w.n0) == (20609, 20353, 1, "fp32", 5.0, 128)
+    A.workload = "nuft3d_recovered"
+    w, nrhs, mode, *_ = bench.pick_workload(A)
+    assert w.recovered and (w.nx, w.w_kind, nrhs, mode) == (64 ** 3, "random", 1, "fp32")
+    A.workload = "fio2d_paper"
+    w, nrhs, mode, *_ = bench.pick_workload(A)
+    X, W, bx, bw = w.points()
+    assert w.recovered and w.tol == 1e-9 and w.N == 1024 ** 2 and W.max() < 1.0 and W.min() >= 0.0
 
 
 def test_sampled_direct_error_rectangular():

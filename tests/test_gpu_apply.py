@@ -233,3 +233,42 @@ def test_accurate_phase_rejections():
     x = torch.zeros(fac.nw, dtype=torch.complex64, device="cuda")
     with pytest.raises(mb.MidbfError):
         mb.apply_batched([dp], [x], [0])
+
+
+def _paper_grid_case():
+    """Example 1 on the paper's grid (X and Omega both in [0,1)^2), n = 32, ID
+    tolerance 1e-9: ranks of ~10-30, so every stage takes the narrow-ID kernels."""
+    if "paper_n32" not in _CACHE:
+        X, W = synth.uniform_grid(32, 2), synth.uniform_grid(32, 2)
+        fac = midbf.build(OPhase(synth.PHASE_FIO2D, X, W), n0=16, tol=1e-9, t=2.0,
+                          boxX=(np.zeros(2), 1.0), boxW=(np.zeros(2), 1.0))
+        _CACHE["paper_n32"] = (fac, mb.Plan.load(planio.write(fac)), midbf.factor_matrices(fac))
+    return _CACHE["paper_n32"]
+
+
+@pytest.mark.parametrize("prec", [mb.FP64, mb.FP32])
+def test_narrow_id_kernels_match_oracle(prec):
+    """One RHS on low-rank factors: the narrow-ID kernels (a warp per ID for
+    the row pattern, a lane per column for the column pattern) against the
+    oracle, by default on the paper-grid plan and forced on every stage of a
+    plan whose ranks reach 64."""
+    fac, plan, mats = _paper_grid_case()
+    dp = mb.DevicePlan(plan, prec)
+    f = synth.complex_gaussian(fac.nw, 1, 50)[:, 0]
+    y = synth.complex_gaussian(fac.nx, 1, 51)[:, 0]
+    g = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec))).cpu().numpy()
+    a = dp.apply(torch.from_numpy(y).to("cuda", _dt(prec)), adjoint=True).cpu().numpy()
+    _check(g, midbf.apply(fac, f, mats), TOL[prec], "paper grid forward")
+    _check(a, midbf.apply_adjoint(fac, y, mats), TOL[prec], "paper grid adjoint")
+    fac, plan, mats = oracle_case("fio2d_n32_L3")
+    dp = mb.DevicePlan(plan, prec)
+    ns = len(dp.stage_info())
+    for q in range(ns):
+        if dp.stage_info()[q][0] != 1:
+            for adj in (0, 1):
+                dp.set_choice(1, q, adj, mb.CHOICE_NARROW)
+    f = synth.complex_gaussian(fac.nw, 1, 52)[:, 0]
+    g = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec))).cpu().numpy()
+    a = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec)), adjoint=True).cpu().numpy()
+    _check(g, midbf.apply(fac, f, mats), TOL[prec], "forced narrow forward")
+    _check(a, midbf.apply_adjoint(fac, f, mats), TOL[prec], "forced narrow adjoint")
