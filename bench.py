@@ -83,7 +83,7 @@ def parse():
     ap.add_argument("--tune", default=None, choices=["on", "off"],
                     help="run the autotuner for the RHS count before timing (default: on for fio2d_jump)")
     ap.add_argument("--graph", default=None, choices=["on", "off"],
-                    help="time the step as one CUDA-graph replay (default: on for fio2d_jump and the one-RHS fio2d step)")
+                    help="time the step as one CUDA-graph replay (default: on for fio2d_jump and the one-RHS steps)")
     ap.add_argument("--store", default=None, choices=["fp64", "fp32"],
                     help="host storage of the IDs' coefficients (default fp64; fp32 for fio2d_jump, whose "
                          "n = 1024 plan does not fit host memory in FP64)")
@@ -178,9 +178,11 @@ def pick_workload(args):
     store = args.store if args.store is not None else ("fp32" if args.workload == "fio2d_jump" else "fp64")
     jump = args.workload == "fio2d_jump"
     tune = (args.tune or ("on" if jump else "off")) == "on"
-    # the step as one CUDA-graph replay: the default for the one-RHS headline (its 14
-    # launches cost ~2% of the step when issued one by one) and for the n = 1024 plan
-    graph = (args.graph or ("on" if jump or (args.workload == "fio2d" and nrhs == 1) else "off")) == "on"
+    # the step as one CUDA-graph replay: the default for the one-RHS steps of one plan
+    # (the headline's 14 launches cost ~2% of its step when issued one by one, and a
+    # larger share of the shorter Example 2 and 3 steps) and for the n = 1024 plan
+    one_rhs = nrhs == 1 and args.workload in ("fio2d", "nuft3d", "nuft3d_recovered", "fio2d_paper", "helmholtz")
+    graph = (args.graph or ("on" if jump or one_rhs else "off")) == "on"
     return w, nrhs, mode, build, store, tune, graph
 
 
@@ -188,7 +190,7 @@ def pick_workload(args):
 # capture of the kernel as it stands, keyed by (workload, direction, stage index in
 # launch order, stage kind); summaries under profiles/.
 NCU_TRAFFIC = {
-    ("fio2d_n256", "adj", 4, 0): (1.6225e9, "profiles/k_pattern_c1_fio2d_n256_full.md"),
+    ("fio2d_n256", "adj", 4, 0): (1.6254e9, "profiles/k_pattern_c1_fio2d_n256_full.md"),
     ("fio2d_n256", "fwd", 2, 0): (1.6241e9, "profiles/k_pattern_fio2d_n256_full.md"),
     ("fio2d_n256", "fwd", 3, 1): (0.0169e9, "profiles/k_s_fly_fio2d_n256_full.md"),
 }

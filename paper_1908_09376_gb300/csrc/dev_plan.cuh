@@ -127,6 +127,7 @@ struct midbf_dplan {
     int64_t nx = 0, nw = 0;
     int64_t max_space = 0;        // longest internal vector space
     size_t factor_bytes = 0, index_bytes = 0;
+    size_t pad_bytes = 0;   // of factor_bytes: the zero padding of the T columns (not algorithmic)
     size_t tc_image_bytes = 0;    // dense BF16 tile images (tensor-core modes)
     int max_tc_chunks = 0;        // most B-image chunks of one tensor-core stage launch
     std::vector<void*> allocs;

@@ -224,6 +224,11 @@ void group_items(std::vector<It>& items, const std::vector<int>& chunk_of_block,
     for (int k = 0; k < nch; ++k) off[k + 1] += off[k];
 }
 
+// Column stride of T on the device: k rounded up to even, so that every
+// column starts on a 16-byte boundary (the one-RHS column kernel copies 16
+// bytes at a time); the padding entries are zero.
+inline int even_up(int k) { return k + (k & 1); }
+
 // Build the device arrays of an ID stage (V or U), or of a stored S stage
 // seen as dense blocks with no skeleton.
 template <class R>
@@ -236,15 +241,18 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     std::vector<ItemC> items_c, items_c1;
     // T goes to the device in chunks through a bounded host buffer: the
     // largest stages hold billions of entries
-    size_t nt = 0;
+    size_t nt = 0, nt_pad = 0;   // entries of T with its column padding; the padding alone
     {
         size_t ns = 0, nk = 0;
         for (const Block& bk : st.blocks) {
             if (stored_s) {
-                nt += bk.out_idx.size() * bk.in_idx.size();
+                const int k = (int)bk.out_idx.size();
+                nt += (size_t)even_up(k) * bk.in_idx.size();
+                nt_pad += (size_t)(even_up(k) - k) * bk.in_idx.size();
             } else {
                 for (const Sub& sb : bk.subs) {
-                    nt += (size_t)sb.k * (size_t)(sb.m - sb.k);
+                    nt += (size_t)even_up(sb.k) * (size_t)(sb.m - sb.k);
+                    nt_pad += (size_t)(even_up(sb.k) - sb.k) * (size_t)(sb.m - sb.k);
                     nk += (size_t)sb.k;
                     ns += (size_t)(sb.m - sb.k);
                 }
@@ -261,6 +269,7 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
             fail(MIDBF_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
         dp->allocs.push_back(dT);
         dp->factor_bytes += bytes;
+        dp->pad_bytes += nt_pad * sizeof(cx<R>);
     }
     std::vector<cx<R>> T;
     T.reserve(std::min(nt, kChunk + 4096));
@@ -291,16 +300,17 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
             // dense block: one "sub" with k = nrow rows, all columns redundant
             SubDesc sd{};
             sd.k = (int)bk.out_idx.size();
+            sd.ld = even_up(sd.k);
             sd.nskel = 0;
             sd.skel_off = (int)skel.size();
             sd.red_off = (int)red.size();
             sd.narrow_off = noff;
             sd.block = (int)b;
-            if (T.size() + (size_t)sd.k * bd.m > kChunk) flush();
+            if (T.size() + (size_t)sd.ld * bd.m > kChunk) flush();
             sd.t_off = (long long)(t_done + T.size());
             for (int j = 0; j < bd.m; ++j) red.push_back(j);
             const size_t base = T.size();
-            T.resize(base + (size_t)sd.k * bd.m);
+            T.resize(base + (size_t)sd.ld * bd.m);   // the padding rows stay zero
             const int nthreads = std::max(1u, std::thread::hardware_concurrency());
             std::vector<std::thread> th;
             for (int w = 0; w < nthreads; ++w)
@@ -308,7 +318,7 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
                     for (int j = w; j < bd.m; j += nthreads)
                         for (int i = 0; i < sd.k; ++i) {
                             cplx kv = pl.phase.kernel(bk.xidx[i], bk.widx[j]);
-                            T[base + (size_t)j * sd.k + i] = {(R)kv.real(), (R)kv.imag()};
+                            T[base + (size_t)j * sd.ld + i] = {(R)kv.real(), (R)kv.imag()};
                         }
                 });
             for (auto& t : th) t.join();
@@ -319,12 +329,13 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
             for (const Sub& sb : bk.subs) {
                 SubDesc sd{};
                 sd.k = sb.k;
+                sd.ld = even_up(sb.k);
                 sd.nskel = sb.k;
                 sd.skel_off = (int)skel.size();
                 sd.red_off = (int)red.size();
                 sd.narrow_off = noff;
                 sd.block = (int)b;
-                if (T.size() + (size_t)sb.k * (sb.m - sb.k) > kChunk) flush();
+                if (T.size() + (size_t)sd.ld * (sb.m - sb.k) > kChunk) flush();
                 sd.t_off = (long long)(t_done + T.size());
                 noff += sb.k;
                 for (int v : sb.skel) skel.push_back(v);
@@ -333,11 +344,13 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
                 std::iota(perm.begin(), perm.end(), 0);
                 std::sort(perm.begin(), perm.end(), [&](int a, int c) { return sb.red[a] < sb.red[c]; });
                 for (int jj = 0; jj < nred; ++jj) red.push_back(sb.red[perm[jj]]);
-                for (int jj = 0; jj < nred; ++jj)
+                for (int jj = 0; jj < nred; ++jj) {
                     for (int i = 0; i < sb.k; ++i) {
                         const cplx v = sb.t((size_t)i * nred + perm[jj]);
                         T.push_back({(R)v.real(), (R)v.imag()});
                     }
+                    if (sd.ld > sb.k) T.push_back({R(0), R(0)});   // pad the column to ld entries
+                }
                 subs.push_back(sd);
                 maxk = std::max(maxk, sb.k);
                 max_nred = std::max(max_nred, (size_t)nred);
@@ -659,7 +672,7 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out,
         ds.out_len = st.out_len;
         ds.in_user = s == 0;
         ds.out_user = st.out_user != 0;
-        const size_t f0 = dp->factor_bytes, i0 = dp->index_bytes;
+        const size_t f0 = dp->factor_bytes, i0 = dp->index_bytes, p0 = dp->pad_bytes;
         if (st.kind == KIND_S) {
             if (dp->s_mode == MIDBF_S_STORED) make_id_stage<R>(dp, pl, st, ds, true, ck, nch);
             else make_s_stage<R>(dp, pl, st, ds, ck, nch);
@@ -677,8 +690,10 @@ void make_stages(midbf_dplan* dp, const Plan& pl, std::vector<DevStage<R>>& out,
             }
         }
         // algorithmic bytes: factor data and position maps once, vectors per RHS
-        // (work-item lists and descriptors are bookkeeping, counted too)
-        dp->stage_fixed_bytes.push_back((double)(dp->factor_bytes - f0) + (double)(dp->index_bytes - i0));
+        // (work-item lists and descriptors are bookkeeping, counted too; the zero
+        // padding of the T columns is not)
+        dp->stage_fixed_bytes.push_back((double)(dp->factor_bytes - f0) - (double)(dp->pad_bytes - p0) +
+                                        (double)(dp->index_bytes - i0));
         dp->stage_vec_entries.push_back(in_len + st.out_len);
         dp->stage_kind.push_back(st.kind);
         int64_t ent = 0, dense = 0;

@@ -52,17 +52,18 @@ def test_workload_defaults():
     assert bench.pick_workload(A)[6] is False      # the graph default is for the one-RHS step only
     A.nrhs = None
     A.workload = "fio3d_n32"
-    w, nrhs, mode, *_ = bench.pick_workload(A)
-    assert (w.d, w.N, nrhs, mode) == (3, 32768, 256, "bf16r")
+    w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
+    assert (w.d, w.N, nrhs, mode, graph) == (3, 32768, 256, "bf16r", False)
     A.workload = "fio2d_jump"
     w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
     assert (w.N, nrhs, mode, store, tune, graph) == (1024 * 1024, 16, "fp32", "fp32", True, True)
     A.workload, A.n = "nuft3d", None
-    w, nrhs, mode, *_ = bench.pick_workload(A)
+    w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
     assert (w.d, w.nx, w.nw, nrhs, mode, w.x_kind, w.w_kind) == (3, 64 ** 3, 64 ** 3, 1, "fp32", "random", "random")
+    assert graph                                  # every one-RHS step of one plan is replayed as a graph
     A.workload = "helmholtz"
-    w, nrhs, mode, *_ = bench.pick_workload(A)
-    assert (w.nx, w.nw, nrhs, mode, w.t, w.n0) == (20609, 20353, 1, "fp32", 5.0, 128)
+    w, nrhs, mode, build, store, tune, graph = bench.pick_workload(A)
+    assert (w.nx, w.nw, nrhs, mode, w.t, w.n0, graph) == (20609, 20353, 1, "fp32", 5.0, 128, True)
     A.workload = "nuft3d_recovered"
     w, nrhs, mode, *_ = bench.pick_workload(A)
     assert w.recovered and (w.nx, w.w_kind, nrhs, mode) == (64 ** 3, "random", 1, "fp32")
