@@ -190,8 +190,8 @@ def pick_workload(args):
 # capture of the kernel as it stands, keyed by (workload, direction, stage index in
 # launch order, stage kind); summaries under profiles/.
 NCU_TRAFFIC = {
-    ("fio2d_n256", "adj", 4, 0): (1.6254e9, "profiles/k_pattern_c1_fio2d_n256_full.md"),
-    ("fio2d_n256", "fwd", 2, 0): (1.6241e9, "profiles/k_pattern_fio2d_n256_full.md"),
+    ("fio2d_n256", "adj", 4, 0): (1.6237e9, "profiles/k_pattern_c1_fio2d_n256_full.md"),
+    ("fio2d_n256", "fwd", 2, 0): (1.6268e9, "profiles/k_pattern_fio2d_n256_full.md"),
     ("fio2d_n256", "fwd", 3, 1): (0.0169e9, "profiles/k_s_fly_fio2d_n256_full.md"),
 }
 
@@ -294,6 +294,25 @@ def _bf16_peak():
 
 PEAK_BF16 = _bf16_peak()
 PEAK_BF16_SOURCE = "measured (burst)" if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else "fallback"
+
+
+def live_copy_gbps(dev, stream, nbytes=1 << 30, reps=5):
+    """HBM copy rate of this GPU now: read + write bytes of one device-to-device
+    copy over the best of `reps` event-timed copies."""
+    import torch
+    a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    b = torch.empty_like(a)
+    b.copy_(a)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        e0.record(stream)
+        b.copy_(a)
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) * 1e-3)
+    del a, b
+    return 2 * nbytes / best / 1e9
 
 
 def peaks():
@@ -909,6 +928,7 @@ def main():
     sfu_ops = 3 if wl.phase in (synth.PHASE_FIO2D, synth.PHASE_FIO3D, synth.PHASE_FIO2D_JUMP,
                                 synth.PHASE_DISTANCE) and not wl.recovered else 2
     fma_rate, sfu_rate, dfma_rate = mb.pipe_rates(stream)   # measured on this GPU (midbf_pipe_rates)
+    copy_live = live_copy_gbps(dev, stream)
     sfu_peak = sfu_rate / sfu_ops / 1e9             # G entries/s
     s_entries_of = {q_: sinfo[q_][1] for q_ in range(ns) if sinfo[q_][0] == 1}
 
@@ -1240,6 +1260,9 @@ def main():
                        "note": "middle factor and its U stage run chunk by chunk on two streams (midbf_dplan_set_overlap)"},
            "pipe_rates": {"fma_per_s": fma_rate, "sfu_per_s": sfu_rate, "fp64_fma_per_s": dfma_rate,
                           "source": "midbf_pipe_rates, measured"},
+           "hbm_copy_live": {"GBps": round(copy_live, 1),
+                             "how": "device-to-device copy of 1 GiB in this process (read + write bytes), best of 5; "
+                                    "context for this GPU's HBM beside the roofline's peak"},
            "clocks": clk, "e2e": e2e,
            "gpu_launches": args.steps * 2 * launches_per_apply, "cpu_baseline": cpu}
     out.update(extras)

@@ -333,7 +333,10 @@ int midbf_apply_host(const midbf_dplan* dp, int adjoint, const void* in_host, vo
  * together on one stream.  Level index q of every instance goes into one
  * group of launches (forward instances run their stage q, adjoint instances
  * their stage ns-1-q), so the number of launches grows with the number of
- * levels and kernel variants, not with count.  All dplans must share one
+ * levels and kernel variants, not with count; a one-RHS instance's stage
+ * that the single-instance apply runs on the narrow-ID or cluster kernels
+ * gets that launch of its own, so every output equals the single-instance
+ * apply's (tuned SIMT tiles included) bit for bit.  All dplans must share one
  * precision and device; in[i]/out[i] are device vectors with leading
  * dimensions ldin[i]/ldout[i] as in midbf_apply; no two instances may share
  * an output.  workspace: device memory of midbf_batched_workspace_size bytes.
@@ -435,7 +438,13 @@ void midbf_graph_destroy(midbf_graph* graph);
                                     a lane per column (columns); the default for
                                     stages whose ranks are all <= 48 (and, for
                                     the rows, whose IDs have <= 128 redundant
-                                    columns) */
+                                    columns and number >= 32 per SM) */
+#define MIDBF_CHOICE_CLUSTER 128 /* one RHS, a V stage forward or a U stage adjoint:
+                                    a thread-block cluster of up to 8 CTAs per
+                                    work item, splitting its columns, the partial
+                                    sums added through distributed shared memory
+                                    in a fixed order; the default for such stages
+                                    with fewer than 6 work items per SM */
 int midbf_autotune(midbf_dplan* dp, int nrhs, void* stream);
 int midbf_set_choice(midbf_dplan* dp, int nrhs, int stage, int adjoint, int choice);
 int midbf_get_choice(const midbf_dplan* dp, int nrhs, int stage, int adjoint, int* choice);

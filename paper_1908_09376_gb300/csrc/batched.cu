@@ -180,6 +180,11 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
     for (int q = 0; q < maxst; ++q) {
         struct Entry { int i, sidx; VecRef<R> src, dst; };
         std::map<std::array<int, 4>, std::vector<Entry>> groups;
+        // one-RHS ID stages that the single-instance apply runs on the narrow-ID
+        // or cluster kernels run the same launch here (one per instance), so
+        // every output equals the single-instance apply's bit for bit
+        struct Solo { Entry e; const DevStage<R>* ds; bool use_r, narrow; int cl; };
+        std::vector<Solo> solo;
         for (int i = 0; i < count; ++i) {
             const auto& sts = stages_of<R>(dps[i]);
             const int ns = (int)sts.size();
@@ -199,6 +204,15 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
             if (ds.id) {
                 const bool wide_is_fwd_input = ds.kind != KIND_U;
                 const bool use_r = adj ? !wide_is_fwd_input : wide_is_fwd_input;
+                if (nr == 1) {
+                    const int ch = tuned_choice(dps[i], nr, sidx, adj);
+                    const bool narrow = use_narrow(ds, 1, ch, use_r);
+                    const int cl = (use_r && !narrow) ? row_cluster_for(ds, ch) : 1;
+                    if (narrow || cl > 1) {
+                        solo.push_back({e, &ds, use_r, narrow, cl});
+                        continue;
+                    }
+                }
                 if (use_r) {
                     const int t = forced_or_pick<R>(force, nr, [&](int qq) { return pattern_r_smem<R>(ds.max_nred, ds.rt, qq); });
                     key = {BT_R, ds.rt, t, 0};
@@ -226,6 +240,15 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
                 if (!dry) launch_batch_group<R>(dps, key, &ents[g0], n, nrhs, adjoint, s);
                 ++launches;
             }
+        }
+        for (const Solo& o : solo) {
+            if (!dry) {
+                const bool conj = adjoint[o.e.i] != 0;
+                if (o.cl > 1) launch_r_cluster<R>(*o.ds, o.e.src, o.e.dst, conj, o.cl, s);
+                else if (o.use_r) launch_r_narrow<R>(*o.ds, o.e.src, o.e.dst, conj, s);
+                else launch_c_narrow<R>(*o.ds, o.e.src, o.e.dst, conj, s);
+            }
+            ++launches;
         }
     }
     return launches;

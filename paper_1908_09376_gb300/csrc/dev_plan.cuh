@@ -69,8 +69,11 @@ struct DevStage : DevStageBase {
     IdStage<R> ids{};
     IdStage<R> ids1{};   // same data, items for the one-RHS pattern-C kernel
     int n_items_r = 0, n_items_c = 0, n_items_c1 = 0, rt = 1;
+    int range_c1 = kRangeC1;   // outputs per one-RHS column item (smaller for stages of few wide blocks)
+    int row_cl = 1;            // CTAs per cluster of the one-RHS row pattern by default (1: no cluster)
     int n_subs = 0, max_k = 0;          // interpolative decompositions of the stage, their largest rank
     int max_nred = 0, max_narrow = 0, max_nsub = 1;
+    int n_blocks = 0, max_m = 0;        // blocks of an ID stage, their largest wide size
     // on-the-fly S
     SStage<R> ss{};
     SSide<R> srows{}, scols{};
@@ -199,18 +202,27 @@ void launch_wait_selftest(int* status, int ctas, cudaStream_t s);
 
 constexpr int kNarrowK = 48;      // one RHS: the narrow-ID kernels for stages whose ranks are all <= this
 constexpr int kNarrowRed = 128;   // and (row pattern) whose IDs have at most this many redundant columns
+constexpr int kNarrowWarps = 32;  // and (row pattern) at least this many IDs (one warp each) per SM
+constexpr int kClusterCtasPerSm = 6;  // one RHS, row pattern: clusters when a stage has fewer items per SM
+constexpr int kWarpBlocksPerSm = 16;  // narrow column pattern: a warp per block from this many blocks per SM
+constexpr size_t kWarpBlockSmem = 64 * 1024;   // and while a CTA's 8 blocks fit this much shared memory
+constexpr int kMaxRowCluster = 8;     // CTAs per cluster (the portable limit)
 constexpr int kTcMinRhs = 16;     // tensor cores for the middle factor from this many RHS on
 constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
 
 
 // SIMT RHS tile named by a choice (0: none).
+inline bool whole_choice(int choice) {   // a choice that takes no MIDBF_CHOICE_PERSIST bit
+    return choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW || choice == MIDBF_CHOICE_CLUSTER;
+}
+
 inline int choice_tile(int choice) {
-    const int base = (choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW) ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
+    const int base = whole_choice(choice) ? 0 : (choice & ~MIDBF_CHOICE_PERSIST);
     return base >= 1 && base <= 16 ? base : 0;
 }
 
 inline bool valid_choice(int choice) {
-    if (choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW) return true;
+    if (whole_choice(choice)) return true;
     const int base = choice & ~MIDBF_CHOICE_PERSIST;
     return base == MIDBF_CHOICE_DEFAULT || base == MIDBF_CHOICE_COLUMN1 || base == 1 || base == 2 || base == 4 ||
            base == 8 || base == 16;
@@ -219,17 +231,43 @@ inline bool valid_choice(int choice) {
 // Whether a one-RHS ID-stage launch takes the narrow-ID kernels: asked for
 // (MIDBF_CHOICE_NARROW), or by default when every rank is at most kNarrowK
 // and, for the row pattern (a warp walks all the redundant columns of its ID
-// alone), every ID has at most kNarrowRed redundant columns; never for a
-// stage prepared for the overlap (those launch chunks of items).  Measured
-// on one GB300: the paper-grid plan of Example 1 (ranks ~11, ~33 redundant
-// columns) runs its stages in about half the time, while Example 2's leaf
-// IDs (rank 44, 468 redundant columns) ran 5x slower in the row pattern,
-// with too few warps for the serial column walk.
+// alone), every ID has at most kNarrowRed redundant columns and the stage has
+// at least kNarrowWarps IDs per SM; never for a stage prepared for the
+// overlap (those launch chunks of items).  Measured on one GB300: the
+// paper-grid plan of Example 1 at n = 1024 (ranks ~11, ~33 redundant
+// columns, 16,384 IDs per stage) runs its stages in about half the time;
+// Example 2's leaf IDs (rank 44, 468 redundant columns) ran 5x slower in the
+// row pattern, with too few warps for the serial column walk, and so did the
+// n = 256 paper-grid plan (1,024 IDs per stage: 7 warps per SM) by 3-4x.
 template <class R>
 inline bool use_narrow(const DevStage<R>& ds, int nrhs, int choice, bool row_pattern) {
     if (nrhs != 1 || !ds.id || ds.nchunks != 0 || ds.max_k > 64) return false;
     if (choice == MIDBF_CHOICE_NARROW) return true;
-    return choice == MIDBF_CHOICE_DEFAULT && ds.max_k <= kNarrowK && (!row_pattern || ds.max_nred <= kNarrowRed);
+    return choice == MIDBF_CHOICE_DEFAULT && ds.max_k <= kNarrowK &&
+           (!row_pattern || (ds.max_nred <= kNarrowRed && ds.n_subs >= kNarrowWarps * sm_count()));
+}
+
+// Cluster size of the one-RHS row pattern for a stage of n_items row items
+// whose IDs have at most max_nred redundant columns: 1 when the stage has
+// kClusterCtasPerSm items per SM or more, else enough CTAs per item to reach
+// that, at most kMaxRowCluster and with ~4 columns per warp at least.  Fixed
+// per stage when the plan is made, so every launch of the stage (whole, by
+// chunks, or in a batch) splits the columns alike.
+inline int row_cluster_size(int n_items, int max_nred) {
+    const int target = kClusterCtasPerSm * sm_count();
+    if (n_items <= 0 || n_items >= target) return 1;
+    int cl = std::min(kMaxRowCluster, (target + n_items - 1) / n_items);
+    while (cl > 1 && max_nred < 4 * kWarps * cl) --cl;
+    return cl;
+}
+
+// The cluster size of a one-RHS row-pattern launch of stage ds under a choice:
+// the stage's default size, at least 2 when asked for (MIDBF_CHOICE_CLUSTER),
+// 1 under any other choice.
+template <class R>
+inline int row_cluster_for(const DevStage<R>& ds, int choice) {
+    if (choice == MIDBF_CHOICE_CLUSTER) return std::max(2, ds.row_cl);
+    return choice == MIDBF_CHOICE_DEFAULT ? ds.row_cl : 1;
 }
 
 // Internal vectors of the workspace: the two ping-pong vectors, and a third
@@ -263,6 +301,8 @@ void launch_c(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
               bool persist = false);
 template <class R>
 void launch_r_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s);
+template <class R>
+void launch_r_cluster(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, int cl, cudaStream_t s);
 template <class R>
 void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s);
 template <class R>

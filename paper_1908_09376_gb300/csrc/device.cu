@@ -361,9 +361,35 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
         max_narrow = std::max(max_narrow, (size_t)bd.nnarrow);
         blocks.push_back(bd);
         for (int o0 = 0; o0 < bd.m; o0 += kRangeC) items_c.push_back({(int)b, o0, std::min(bd.m, o0 + kRangeC), 0});
-        for (int o0 = 0; o0 < bd.m; o0 += kRangeC1) items_c1.push_back({(int)b, o0, std::min(bd.m, o0 + kRangeC1), 0});
     }
     if (max_nsub > 16) fail(MIDBF_EINTERNAL, "more than 16 sub-blocks in a block");
+    // One-RHS column items: kRangeC1 outputs each, or fewer when a stage has
+    // too few wide blocks to give every SM several items (a CTA streams one
+    // item's columns at a latency-bound rate, so a short grid leaves the HBM
+    // idle); ranges of 64 or 32 outputs split the same columns over more CTAs.
+    // Every item gathers all of its block's narrow inputs, so a range is
+    // halved only while those gathers stay within 1/8 of the stage's T
+    // entries (a block with little T, mostly skeleton, keeps its range).
+    {
+        const int target = 4 * sm_count();
+        int range = kRangeC1;
+        auto count = [&](int rg) {
+            size_t c = 0;
+            for (const BlockDesc& bd : blocks) c += (size_t)((bd.m + rg - 1) / rg);
+            return c;
+        };
+        auto gathers = [&](int rg) {
+            size_t g = 0;
+            for (const BlockDesc& bd : blocks) g += (size_t)bd.nnarrow * (size_t)((bd.m + rg - 1) / rg);
+            return g;
+        };
+        const size_t t_stage = nt - nt_pad;
+        while (range > 32 && count(range) < (size_t)target && 8 * gathers(range / 2) <= t_stage) range /= 2;
+        for (size_t b = 0; b < blocks.size(); ++b)
+            for (int o0 = 0; o0 < blocks[b].m; o0 += range)
+                items_c1.push_back({(int)b, o0, std::min(blocks[b].m, o0 + range), 0});
+        ds.range_c1 = range;
+    }
     const int rt = rows_per_lane(maxk);
     for (size_t s = 0; s < subs.size(); ++s)
         for (int r0 = 0; r0 < subs[s].k; r0 += 32 * rt) items_r.push_back({(int)s, r0});
@@ -373,14 +399,34 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
         group_items(items_c1, *chunk_of_block, nch, [](const ItemC& it) { return it.block; }, ds.ck_c1);
         ds.nchunks = nch;
     }
+    // the column range of every (column item, sub-block): one host-side binary
+    // search over the sorted redundant indices, instead of one per CTA
+    auto make_jr = [&](std::vector<ItemC>& items) {
+        std::vector<int2> jr;
+        for (ItemC& it : items) {
+            const BlockDesc& bd = blocks[it.block];
+            it.jr_off = (int)jr.size();
+            for (int c = 0; c < bd.nsub; ++c) {
+                const SubDesc& sd = subs[bd.sub0 + c];
+                const int* r = red.data() + sd.red_off;
+                const int* e = r + (bd.m - sd.nskel);
+                jr.push_back(make_int2((int)(std::lower_bound(r, e, it.o0) - r), (int)(std::lower_bound(r, e, it.o1) - r)));
+            }
+        }
+        return jr;
+    };
+    const std::vector<int2> jr_c = make_jr(items_c), jr_c1 = make_jr(items_c1);
     ds.id = true;
     ds.rt = rt;
     ds.n_subs = (int)subs.size();
     ds.max_k = maxk;
     ds.n_items_r = (int)items_r.size();
+    ds.row_cl = row_cluster_size(ds.n_items_r, (int)max_nred);
     ds.n_items_c = (int)items_c.size();
     ds.max_nred = (int)max_nred;
     ds.max_narrow = (int)max_narrow;
+    ds.n_blocks = (int)blocks.size();
+    for (const BlockDesc& bd : blocks) ds.max_m = std::max(ds.max_m, bd.m);
     ds.max_nsub = (int)max_nsub;
     if (pattern_r_smem<R>((int)max_nred, rt, 1) > kSmemCap || pattern_c_smem<R>((int)max_narrow, (int)max_nsub, kRangeC, 1) > kSmemCap)
         fail(MIDBF_EINTERNAL, "block too wide for shared memory");
@@ -395,8 +441,10 @@ void make_id_stage(midbf_dplan* dp, const Plan& pl, const Stage& st, DevStage<R>
     ds.ids.T = dT;
     ds.ids.items_r = upload(dp, items_r, &dp->index_bytes);
     ds.ids.items_c = upload(dp, items_c, &dp->index_bytes);
+    ds.ids.jr = upload(dp, jr_c, &dp->index_bytes);
     ds.ids1 = ds.ids;
     ds.ids1.items_c = upload(dp, items_c1, &dp->index_bytes);
+    ds.ids1.jr = upload(dp, jr_c1, &dp->index_bytes);
     ds.n_items_c1 = (int)items_c1.size();
     if constexpr (sizeof(R) == 4) {
         if (dp->tc_mode && !stored_s) make_tc_images<R>(dp, st, ds);
@@ -774,8 +822,10 @@ int grid_for(const void* kernel, size_t smem, int nitems, bool persist) {
 // One stage launch.  choice: MIDBF_CHOICE_DEFAULT (the built-in rules: tensor
 // cores in the BF16 modes from kTcMinRhs / kTcBlkMinRhs RHS on, else the SIMT
 // kernel with the RHS tile of pick_nr), a SIMT RHS tile (1, 2, 4, 8, 16) or
-// MIDBF_CHOICE_COLUMN1 (the one-RHS pattern-C kernel), optionally with
-// MIDBF_CHOICE_PERSIST, or MIDBF_CHOICE_TENSOR.
+// MIDBF_CHOICE_COLUMN1 (the one-RHS pattern-C kernel), each optionally with
+// MIDBF_CHOICE_PERSIST; or one of MIDBF_CHOICE_NARROW (the narrow-ID
+// kernels), MIDBF_CHOICE_CLUSTER (the one-RHS row pattern on clusters of
+// CTAs) and MIDBF_CHOICE_TENSOR.
 template <class R>
 void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, VecRef<R> src, VecRef<R> dst, int nrhs,
                   int choice, __nv_bfloat16* bimg, cudaStream_t s) {
@@ -793,12 +843,16 @@ void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, Ve
     // pattern R computes narrow from wide; pattern C wide from narrow.
     const bool use_r = adjoint ? !wide_is_fwd_input : wide_is_fwd_input;
     const bool narrow = use_narrow(ds, nrhs, choice, use_r);
-    const bool persist = !narrow && choice != MIDBF_CHOICE_TENSOR && (choice & MIDBF_CHOICE_PERSIST) != 0;
+    const bool persist = !whole_choice(choice) && (choice & MIDBF_CHOICE_PERSIST) != 0;
     const int tile = choice_tile(choice);
-    const bool col1 = !narrow && choice != MIDBF_CHOICE_TENSOR &&
-                      (choice & ~MIDBF_CHOICE_PERSIST) == MIDBF_CHOICE_COLUMN1;
+    const bool col1 = !whole_choice(choice) && (choice & ~MIDBF_CHOICE_PERSIST) == MIDBF_CHOICE_COLUMN1;
+    // one RHS, row pattern: a cluster of CTAs per item when asked for, or by
+    // default when the stage has few items
+    const int cl = (ds.id && use_r && !narrow && nrhs == 1) ? row_cluster_for(ds, choice) : 1;
     if (ds.id) {
-        if (narrow) {
+        if (cl > 1) {
+            launch_r_cluster<R>(ds, src, dst, adjoint, cl, s);
+        } else if (narrow) {
             if (use_r) launch_r_narrow<R>(ds, src, dst, adjoint, s);
             else launch_c_narrow<R>(ds, src, dst, adjoint, s);
         } else if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
@@ -963,6 +1017,7 @@ std::vector<int> stage_candidates(const midbf_dplan* dp, const DevStage<R>& ds, 
     if (ds.id && nrhs == 1 && ds.nchunks == 0 && ds.max_k <= 64 &&
         (use_r || pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap))
         c.push_back(MIDBF_CHOICE_NARROW);
+    if (ds.id && use_r && nrhs == 1) c.push_back(MIDBF_CHOICE_CLUSTER);
     if (sizeof(R) == 4 && (ds.id ? ds.tc : dp->tc_mode != 0)) c.push_back(MIDBF_CHOICE_TENSOR);
     return c;
 }

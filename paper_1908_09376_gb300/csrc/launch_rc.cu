@@ -32,6 +32,40 @@ void launch_r_nr(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, 
     }
 }
 
+// The one-RHS cluster form (k_pattern_r_cl): a cluster of cl CTAs per item.
+template <class R, int RT, bool CJ>
+void launch_r_cl_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int cl, cudaStream_t s) {
+    const size_t sm = pattern_r_cl_smem<R>(ds.max_nred, RT);
+    auto kf = k_pattern_r_cl<R, RT, CJ>;
+    set_smem(kf, sm);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ds.n_items_r * (unsigned)cl, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kf, ds.ids, src, dst));
+}
+
+template <class R>
+void launch_r_cluster(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, int cl, cudaStream_t s) {
+    if (ds.n_items_r == 0) return;
+    if (cl < 2 || cl > kMaxRowCluster) fail(MIDBF_EINTERNAL, "row cluster size out of range");
+    if (ds.rt == 1) {
+        if (conj) launch_r_cl_t<R, 1, true>(ds, src, dst, cl, s);
+        else launch_r_cl_t<R, 1, false>(ds, src, dst, cl, s);
+    } else {
+        if (conj) launch_r_cl_t<R, 2, true>(ds, src, dst, cl, s);
+        else launch_r_cl_t<R, 2, false>(ds, src, dst, cl, s);
+    }
+}
+
 template <class R>
 void launch_r(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool conj, cudaStream_t s, int force,
               bool persist) {
@@ -121,6 +155,16 @@ void launch_r_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool c
 template <class R>
 void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool conj, cudaStream_t s) {
     if (ds.n_items_c1 == 0) return;
+    // many small blocks: a warp per block (the same results bit for bit)
+    const int per_warp = ds.max_narrow + ds.max_m;
+    const size_t smw = (size_t)kWarps * per_warp * sizeof(cx<R>);
+    if (ds.n_blocks >= kWarpBlocksPerSm * sm_count() && smw <= kWarpBlockSmem) {
+        auto kw = conj ? k_pattern_c1w<R, true> : k_pattern_c1w<R, false>;
+        set_smem(kw, smw);
+        kw<<<(ds.n_blocks + kWarps - 1) / kWarps, kThreads, smw, s>>>(ds.ids1, src, dst, ds.n_blocks, per_warp);
+        CK(cudaGetLastError());
+        return;
+    }
     const size_t sm = pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1);
     auto kf = conj ? k_pattern_c1n<R, true> : k_pattern_c1n<R, false>;
     set_smem(kf, sm);
@@ -133,6 +177,8 @@ template void launch_r_narrow<double>(const DevStage<double>&, VecRef<double>, V
 template void launch_c_narrow<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, cudaStream_t);
 template void launch_c_narrow<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, bool, cudaStream_t);
 
+template void launch_r_cluster<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, int, cudaStream_t);
+template void launch_r_cluster<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, bool, int, cudaStream_t);
 template void launch_r<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
 template void launch_r<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
 template void launch_c<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);

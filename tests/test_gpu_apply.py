@@ -250,8 +250,9 @@ def _paper_grid_case():
 def test_narrow_id_kernels_match_oracle(prec):
     """One RHS on low-rank factors: the narrow-ID kernels (a warp per ID for
     the row pattern, a lane per column for the column pattern) against the
-    oracle, by default on the paper-grid plan and forced on every stage of a
-    plan whose ranks reach 64."""
+    oracle, by default on the paper-grid plan (its column stages; its row
+    stages have too few IDs per SM and take the cluster kernel) and forced on
+    every stage of a plan whose ranks reach 64."""
     fac, plan, mats = _paper_grid_case()
     dp = mb.DevicePlan(plan, prec)
     f = synth.complex_gaussian(fac.nw, 1, 50)[:, 0]
@@ -261,14 +262,47 @@ def test_narrow_id_kernels_match_oracle(prec):
     _check(g, midbf.apply(fac, f, mats), TOL[prec], "paper grid forward")
     _check(a, midbf.apply_adjoint(fac, y, mats), TOL[prec], "paper grid adjoint")
     fac, plan, mats = oracle_case("fio2d_n32_L3")
-    dp = mb.DevicePlan(plan, prec)
-    ns = len(dp.stage_info())
-    for q in range(ns):
-        if dp.stage_info()[q][0] != 1:
+    # every stage, the stored middle factor included (its blocks are dense
+    # sub-blocks with no skeleton: the narrow kernels add no identity part)
+    for s_mode in (mb.S_ONTHEFLY, mb.S_STORED):
+        dp = mb.DevicePlan(plan, prec, s_mode)
+        for q in range(len(dp.stage_info())):
             for adj in (0, 1):
                 dp.set_choice(1, q, adj, mb.CHOICE_NARROW)
-    f = synth.complex_gaussian(fac.nw, 1, 52)[:, 0]
-    g = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec))).cpu().numpy()
-    a = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec)), adjoint=True).cpu().numpy()
-    _check(g, midbf.apply(fac, f, mats), TOL[prec], "forced narrow forward")
-    _check(a, midbf.apply_adjoint(fac, f, mats), TOL[prec], "forced narrow adjoint")
+        f = synth.complex_gaussian(fac.nw, 1, 52)[:, 0]
+        g = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec))).cpu().numpy()
+        a = dp.apply(torch.from_numpy(f).to("cuda", _dt(prec)), adjoint=True).cpu().numpy()
+        _check(g, midbf.apply(fac, f, mats), TOL[prec], f"forced narrow forward, S mode {s_mode}")
+        _check(a, midbf.apply_adjoint(fac, f, mats), TOL[prec], f"forced narrow adjoint, S mode {s_mode}")
+
+
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("prec,s_mode", [(mb.FP64, mb.S_STORED), (mb.FP32, mb.S_ONTHEFLY), (mb.FP32, mb.S_STORED)])
+def test_cluster_row_kernel_matches_oracle(case, prec, s_mode):
+    """The one-RHS row pattern on thread-block clusters (the CTAs of a cluster
+    split an item's columns; CTA 0 adds the partial rows through distributed
+    shared memory in rank order): forced on every stage and direction it runs
+    (V forward, U adjoint, the stored middle factor forward), against the
+    oracle's apply of the same factors; the result is the same bit for bit on
+    a second call.  With 3 RHS the choice falls back to the SIMT tiles."""
+    fac, plan, mats = oracle_case(case)
+    dp = mb.DevicePlan(plan, prec, s_mode)
+    for q in range(len(dp.stage_info())):
+        for adj in (0, 1):
+            dp.set_choice(1, q, adj, mb.CHOICE_CLUSTER)
+            dp.set_choice(3, q, adj, mb.CHOICE_CLUSTER)
+    f = synth.complex_gaussian(fac.nw, 3, 60)
+    y = synth.complex_gaussian(fac.nx, 3, 61)
+    F = torch.from_numpy(f.T.copy()).to("cuda", _dt(prec))
+    Y = torch.from_numpy(y.T.copy()).to("cuda", _dt(prec))
+    g1, a1 = dp.apply(F[0]), dp.apply(Y[0], adjoint=True)
+    g2, a2 = dp.apply(F[0]), dp.apply(Y[0], adjoint=True)
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2) and torch.equal(a1, a2)
+    _check(g1.cpu().numpy(), midbf.apply(fac, f[:, 0], mats), TOL[prec], f"{case} cluster forward")
+    _check(a1.cpu().numpy(), midbf.apply_adjoint(fac, y[:, 0], mats), TOL[prec], f"{case} cluster adjoint")
+    g3, a3 = dp.apply(F).cpu().numpy().T, dp.apply(Y, adjoint=True).cpu().numpy().T
+    for r in range(3):
+        _check(g3[:, r], midbf.apply(fac, f[:, r], mats), TOL[prec], f"{case} 3 RHS forward")
+        _check(a3[:, r], midbf.apply_adjoint(fac, y[:, r], mats), TOL[prec], f"{case} 3 RHS adjoint")
+    assert dp.status() == mb.OK

@@ -2,7 +2,8 @@
 
 Every stage of an apply can run several kernel variants (SIMT RHS tiles, the
 one-RHS column kernel, each of them one CTA per item or persistent, the
-narrow-ID kernels for one RHS and low ranks, and the tensor-core kernels).  Forcing each variant of
+narrow-ID kernels for one RHS and low ranks, the one-RHS row pattern on
+thread-block clusters, and the tensor-core kernels).  Forcing each variant of
 each stage in turn must reproduce the oracle's FP64 apply of the same
 factors (FP32: 2e-5; tensor cores with refinement: 2e-5; tolerances as in
 test_gpu_apply / test_gpu_tensor), and the autotuner must record, for every
@@ -40,7 +41,7 @@ def _ref(fac, mats, f, adjoint):
 
 @pytest.mark.parametrize("mode,nrhs,choices", [
     (mb.FP32, 1, [1, mb.CHOICE_COLUMN1, 1 | mb.CHOICE_PERSIST, mb.CHOICE_COLUMN1 | mb.CHOICE_PERSIST]),
-    (mb.FP32, 1, [mb.CHOICE_NARROW]),
+    (mb.FP32, 1, [mb.CHOICE_NARROW, mb.CHOICE_CLUSTER]),
     (mb.FP32, 20, [1, 2, 4, 8, 16, 16 | mb.CHOICE_PERSIST]),
     (mb.BF16 | mb.REFINE, 20, [4, 16 | mb.CHOICE_PERSIST, mb.CHOICE_TENSOR]),
 ])
@@ -83,7 +84,7 @@ def test_autotune_records_valid_choices_and_keeps_results(mode, nrhs):
             if ch == mb.CHOICE_TENSOR:
                 assert mode & mb.BF16
                 continue
-            if ch == mb.CHOICE_NARROW:   # the narrow-ID kernels: one RHS, ranks <= 64
+            if ch in (mb.CHOICE_NARROW, mb.CHOICE_CLUSTER):   # narrow-ID or cluster kernels: one RHS
                 assert nrhs == 1
                 continue
             base = ch & ~mb.CHOICE_PERSIST

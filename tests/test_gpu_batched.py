@@ -66,11 +66,18 @@ def test_batched_argument_errors():
 def test_batched_launch_count():
     """midbf_batched_launches: one launch group per level index and kernel
     variant, so the count lies between the deepest plan's stage count and the
-    sum of all stage counts, and stays the same when instances repeat."""
+    sum of all stage counts, and stays the same when instances of several
+    RHS repeat.  A one-RHS instance's stages that run on the narrow-ID or
+    cluster kernels get launches of their own: a repeated one-RHS instance
+    adds at most its own stage count."""
     facs = [_fac(16, 16), _fac(32, 16), _fac(32, 64)]
     dps = [mb.DevicePlan(mb.Plan.load(planio.write(f)), mb.FP32) for f in facs]
     nst = [len(d.stage_info()) for d in dps]
-    n1 = mb.batched_launches(dps, [0, 1, 0], [1, 3, 20])
+    n1 = mb.batched_launches(dps, [0, 1, 0], [2, 3, 20])
     assert max(nst) <= n1 <= sum(nst)
-    n2 = mb.batched_launches(dps + dps, [0, 1, 0] * 2, [1, 3, 20] * 2)
+    n2 = mb.batched_launches(dps + dps, [0, 1, 0] * 2, [2, 3, 20] * 2)
     assert n2 == n1
+    m1 = mb.batched_launches(dps, [0, 1, 0], [1, 3, 20])
+    assert max(nst) <= m1 <= sum(nst)
+    m2 = mb.batched_launches(dps + dps[:1], [0, 1, 0, 0], [1, 3, 20, 1])
+    assert m1 <= m2 <= m1 + nst[0]
