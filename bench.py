@@ -886,14 +886,20 @@ def main():
         no_overlap = {"ms_per_step": round(statistics.mean(t_off), 5), "chunks": overlap_chunks,
                       "speedup_of_overlap": round(statistics.mean(t_off) / ms_per_step, 3)}
     # the same steps again with CUDA events around every stage launch (profiling runs the
-    # stages one after the other, without the overlap)
+    # stages one after the other, without the overlap).  Reading the stage times waits for
+    # the GPU, so before each profiled apply a ~1 ms spin keeps the GPU busy while the host
+    # queues the apply's launches: an event then never waits for a launch the host has not
+    # issued yet, and the times are the kernels' own.  Each stage reports the median of its
+    # launches.
     dp32.profile(True)
     stage_ms = {}
     for i in range(args.steps):
         flush.zero_()
+        torch.cuda._sleep(2_000_000)
         dp32.apply(f, out=g, workspace=ws1)
         for q, (kind, ms, by) in enumerate(dp32.stage_times()):
             stage_ms.setdefault(("fwd", q, kind, by), []).append(ms)
+        torch.cuda._sleep(2_000_000)
         dp32.apply(g, adjoint=True, out=h, workspace=ws1)
         for q, (kind, ms, by) in enumerate(dp32.stage_times()):
             stage_ms.setdefault(("adj", q, kind, by), []).append(ms)
@@ -910,13 +916,13 @@ def main():
         sidx = q if direction == "fwd" else ns - 1 - q
         return 8.0 * sinfo[sidx][1] * R1
 
-    dom = max(stage_ms.items(), key=lambda kv: statistics.mean(kv[1]))
+    dom = max(stage_ms.items(), key=lambda kv: statistics.median(kv[1]))
     (direction, q, kind, by), times = dom
-    dom_ms = statistics.mean(times)
+    dom_ms = statistics.median(times)
     all_bytes = sum(k[3] for k in stage_ms.keys())
     stage_rows = []
     for k, v in sorted(stage_ms.items(), key=lambda kv: (kv[0][0] != "fwd", kv[0][1])):
-        ms_ = statistics.mean(v)
+        ms_ = statistics.median(v)
         row = {"dir": k[0], "stage": k[1], "kind": "VSU"[k[2]], "ms": round(ms_, 4),
                "GB": round(k[3] / 1e9, 4), "GBps": round(k[3] / (ms_ * 1e-3) / 1e9, 1)}
         if tc_active:
@@ -934,8 +940,8 @@ def main():
 
     def hbm_roofline(exclude_s):
         rows = [(k, v) for k, v in stage_ms.items() if not (exclude_s and k[2] == 1)]
-        (d_, q_, kind_, by_), t_ = max(rows, key=lambda kv: statistics.mean(kv[1]))
-        ms_ = statistics.mean(t_)
+        (d_, q_, kind_, by_), t_ = max(rows, key=lambda kv: statistics.median(kv[1]))
+        ms_ = statistics.median(t_)
         a_ = by_ / (ms_ * 1e-3) / 1e9
         return {"bound": "hbm", "achieved": round(a_, 1), "peak": peak, "unit": "GB/s", "frac": round(a_ / peak, 4),
                 "traffic": None, "kernel": f"{d_} stage {q_} ({'VSU'[kind_]})", "peak_source": peak_kind}
@@ -1128,17 +1134,40 @@ def main():
         dp32.apply(F, out=G, workspace=wsR)
         torch.cuda.synchronize()
         kR = 3
-        totR = 0.0
-        for _ in range(kR):
-            flush.zero_()
-            e0.record(stream)
-            dp32.apply(F, out=G, workspace=wsR)
-            dp32.apply(G, adjoint=True, out=H, workspace=wsR)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            totR += e0.elapsed_time(e1)
-        msR = totR / kR
-        extras["nrhs64_fp32"] = {"value": 2 * N * R / (msR * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msR, 3)}
+
+        def time_r64():
+            tot = 0.0
+            for _ in range(kR):
+                flush.zero_()
+                e0.record(stream)
+                dp32.apply(F, out=G, workspace=wsR)
+                dp32.apply(G, adjoint=True, out=H, workspace=wsR)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            return tot / kR
+        msR = time_r64()
+        # the autotuner's choice of kernel variant per stage and direction for 64 RHS
+        t0_ = time.perf_counter()
+        dp32.autotune(R)
+        tuneR = time.perf_counter() - t0_
+        dp32.apply(F, out=G, workspace=wsR)
+        msRt = time_r64()
+        # FP32 FMA roof: 4 FMAs per complex multiply-add of every T and S entry, per RHS,
+        # forward and adjoint, against the measured FMA rate
+        fmaR = 2 * 4 * float(st["t_entries"] + st["s_entries"]) * R
+        extras["nrhs64_fp32"] = {
+            "value": 2 * N * R / (msRt * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msRt, 3),
+            "autotuned": True, "tune_s": round(tuneR, 1),
+            "default_rules": {"value": 2 * N * R / (msR * 1e-3), "ms_per_step": round(msR, 3)},
+            "roofline": {"bound": "alu", "achieved": round(fmaR / (msRt * 1e-3) / 1e12, 2),
+                         "peak": round(fma_rate / 1e12, 2), "unit": "T FP32 FMA/s",
+                         "frac": round(fmaR / (msRt * 1e-3) / fma_rate, 4),
+                         "peak_source": "measured FP32 FMA rate (midbf_pipe_rates)",
+                         "work": "4 FP32 FMAs per complex multiply-add of every T and S entry and RHS, forward and adjoint"}}
+        for q_ in range(len(sinfo)):
+            for a_ in (0, 1):
+                dp32.set_choice(R, q_, a_, mb.CHOICE_DEFAULT)
         # the same with every stage on the tensor cores (BF16 + refinement), at 64 and
         # at 256 RHS (one full pass of the TMEM accumulator); forward and adjoint each
         # timed, and per stage: algorithmic flops (8 per complex multiply-add of the

@@ -13,7 +13,7 @@ void launch_r_t(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, c
         set_smem(kf, sm);
         kf<<<grid_for(reinterpret_cast<const void*>(kf), sm, n, true), kThreads, sm, s>>>(ds.ids, src, dst, nrhs, n);
     } else {
-        auto kf = k_pattern_r<R, RT, NR, CJ>;
+        auto kf = NR >= 16 ? k_pattern_r16<R, RT, NR, CJ> : k_pattern_r<R, RT, NR, CJ>;
         set_smem(kf, sm);
         kf<<<n, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
     }
