@@ -1153,12 +1153,22 @@ def main():
         tuneR = time.perf_counter() - t0_
         dp32.apply(F, out=G, workspace=wsR)
         msRt = time_r64()
+        # the tuned step's stages, event-timed one by one (the spin keeps the GPU ahead of the host)
+        dp32.profile(True)
+        stR = []
+        for adj_ in (False, True):
+            flush.zero_()
+            torch.cuda._sleep(2_000_000)
+            dp32.apply(G if adj_ else F, adjoint=adj_, out=H if adj_ else G, workspace=wsR)
+            for q_, (kind_, ms_, _) in enumerate(dp32.stage_times()):
+                stR.append({"dir": "adj" if adj_ else "fwd", "stage": q_, "kind": "VSU"[kind_], "ms": round(ms_, 3)})
+        dp32.profile(False)
         # FP32 FMA roof: 4 FMAs per complex multiply-add of every T and S entry, per RHS,
         # forward and adjoint, against the measured FMA rate
         fmaR = 2 * 4 * float(st["t_entries"] + st["s_entries"]) * R
         extras["nrhs64_fp32"] = {
             "value": 2 * N * R / (msRt * 1e-3), "unit": "points*RHS/s", "ms_per_step": round(msRt, 3),
-            "autotuned": True, "tune_s": round(tuneR, 1),
+            "autotuned": True, "tune_s": round(tuneR, 1), "stages": stR,
             "default_rules": {"value": 2 * N * R / (msR * 1e-3), "ms_per_step": round(msR, 3)},
             "roofline": {"bound": "alu", "achieved": round(fmaR / (msRt * 1e-3) / 1e12, 2),
                          "peak": round(fma_rate / 1e12, 2), "unit": "T FP32 FMA/s",

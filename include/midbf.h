@@ -439,6 +439,17 @@ void midbf_graph_destroy(midbf_graph* graph);
                                     stages whose ranks are all <= 48 (and, for
                                     the rows, whose IDs have <= 128 redundant
                                     columns and number >= 32 per SM) */
+#define MIDBF_CHOICE_GEMM 512    /* FP32: register-tiled complex GEMMs, 4 x 4
+                                    micro-tiles per thread, RHS in tiles of 64:
+                                    the middle factor made on the fly (each
+                                    64 x 32 tile of S made once into shared
+                                    memory; the default from 128 RHS on with
+                                    the FP32 phase) and the row and column
+                                    patterns of ID stages and of the stored
+                                    middle factor (T copied into shared memory;
+                                    the default from 32 RHS on, the column
+                                    pattern when its IDs have >= 64 redundant
+                                    columns) */
 #define MIDBF_CHOICE_CLUSTER 128 /* one RHS, a V stage forward or a U stage adjoint:
                                     a thread-block cluster of up to 8 CTAs per
                                     work item, splitting its columns, the partial

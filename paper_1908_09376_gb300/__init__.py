@@ -24,6 +24,7 @@ _lib = C.CDLL(LIB_PATH)
 # ---- constants (include/midbf.h) ------------------------------------------
 OK, EINVAL, ENOMEM, ECUDA, ECALLBACK, ERANK, ERECOVERY, ETIMEOUT, EINTERNAL, EFORMAT = 0, -1, -2, -3, -4, -5, -6, -7, -8, -9
 CHOICE_DEFAULT, CHOICE_COLUMN1, CHOICE_PERSIST, CHOICE_TENSOR, CHOICE_NARROW, CHOICE_CLUSTER = 0, 32, 256, 1024, 64, 128
+CHOICE_GEMM = 512
 PHASE_FIO2D, PHASE_FIO3D, PHASE_FIO2D_JUMP, PHASE_DOT, PHASE_ZERO, PHASE_SEPARABLE, PHASE_LOWRANK = 1, 2, 3, 4, 5, 6, 7
 PHASE_DISTANCE = 8
 FP64, FP32, BF16, REFINE = 0, 1, 2, 16

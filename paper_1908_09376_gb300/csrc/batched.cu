@@ -183,7 +183,7 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
         // one-RHS ID stages that the single-instance apply runs on the narrow-ID
         // or cluster kernels run the same launch here (one per instance), so
         // every output equals the single-instance apply's bit for bit
-        struct Solo { Entry e; const DevStage<R>* ds; bool use_r, narrow; int cl; };
+        struct Solo { Entry e; const DevStage<R>* ds; bool use_r, narrow; int cl; bool gemm; };
         std::vector<Solo> solo;
         for (int i = 0; i < count; ++i) {
             const auto& sts = stages_of<R>(dps[i]);
@@ -204,12 +204,16 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
             if (ds.id) {
                 const bool wide_is_fwd_input = ds.kind != KIND_U;
                 const bool use_r = adj ? !wide_is_fwd_input : wide_is_fwd_input;
+                if (use_gemm(ds, nr, tuned_choice(dps[i], nr, sidx, adj), use_r)) {
+                    solo.push_back({e, &ds, use_r, false, 1, true});
+                    continue;
+                }
                 if (nr == 1) {
                     const int ch = tuned_choice(dps[i], nr, sidx, adj);
                     const bool narrow = use_narrow(ds, 1, ch, use_r);
                     const int cl = (use_r && !narrow) ? row_cluster_for(ds, ch) : 1;
                     if (narrow || cl > 1) {
-                        solo.push_back({e, &ds, use_r, narrow, cl});
+                        solo.push_back({e, &ds, use_r, narrow, cl, false});
                         continue;
                     }
                 }
@@ -223,6 +227,10 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
                     key = {BT_C, 0, t, 0};
                 }
             } else {
+                if (use_gemm(ds, nr, tuned_choice(dps[i], nr, sidx, adj), false)) {
+                    solo.push_back({e, &ds, false, false, 1, true});
+                    continue;
+                }
                 const int t = forced_or_pick<R>(force, nr, [&](int qq) {
                     return s_fly_smem<R>(ds.ss.P, ds.ss.Q, qq <= 4 && sizeof(R) == 4 ? 4 : 2, qq);
                 });
@@ -244,7 +252,13 @@ int run_batched(int count, const midbf_dplan* const* dps, const int* adjoint, co
         for (const Solo& o : solo) {
             if (!dry) {
                 const bool conj = adjoint[o.e.i] != 0;
-                if (o.cl > 1) launch_r_cluster<R>(*o.ds, o.e.src, o.e.dst, conj, o.cl, s);
+                if (o.gemm) {
+                    if constexpr (sizeof(R) == 4) {
+                        if (o.ds->id && o.use_r) launch_r_gemm(*o.ds, o.e.src, o.e.dst, nrhs[o.e.i], conj, s);
+                        else if (o.ds->id) launch_c_gemm(*o.ds, o.e.src, o.e.dst, nrhs[o.e.i], conj, s);
+                        else launch_s_gemm(*o.ds, o.e.src, o.e.dst, nrhs[o.e.i], conj, s);
+                    }
+                } else if (o.cl > 1) launch_r_cluster<R>(*o.ds, o.e.src, o.e.dst, conj, o.cl, s);
                 else if (o.use_r) launch_r_narrow<R>(*o.ds, o.e.src, o.e.dst, conj, s);
                 else launch_c_narrow<R>(*o.ds, o.e.src, o.e.dst, conj, s);
             }

@@ -35,6 +35,7 @@ using namespace midbf_dev;
     } while (0)
 
 constexpr int kRangeC = 64;   // output entries per pattern-C item
+static_assert(kRangeC <= midbf_dev::kCgOut, "the column GEMM takes at most kCgOut outputs per item");
 constexpr size_t kSmemCap = 200 * 1024;  // dynamic shared memory budget per CTA
 
 struct DevBuf {
@@ -204,6 +205,8 @@ constexpr int kNarrowK = 48;      // one RHS: the narrow-ID kernels for stages w
 constexpr int kNarrowRed = 128;   // and (row pattern) whose IDs have at most this many redundant columns
 constexpr int kNarrowWarps = 32;  // and (row pattern) at least this many IDs (one warp each) per SM
 constexpr int kClusterCtasPerSm = 6;  // one RHS, row pattern: clusters when a stage has fewer items per SM
+constexpr int kGemmMinRhs = 32;       // FP32 ID stages: the GEMM forms from this many RHS on
+constexpr int kSGemmMinRhs = 128;     // FP32 middle factor on the fly: the GEMM form from this many RHS on
 constexpr int kWarpBlocksPerSm = 16;  // narrow column pattern: a warp per block from this many blocks per SM
 constexpr size_t kWarpBlockSmem = 64 * 1024;   // and while a CTA's 8 blocks fit this much shared memory
 constexpr int kMaxRowCluster = 8;     // CTAs per cluster (the portable limit)
@@ -213,7 +216,27 @@ constexpr int kTcBlkMinRhs = 16;  // and for the V / U stages
 
 // SIMT RHS tile named by a choice (0: none).
 inline bool whole_choice(int choice) {   // a choice that takes no MIDBF_CHOICE_PERSIST bit
-    return choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW || choice == MIDBF_CHOICE_CLUSTER;
+    return choice == MIDBF_CHOICE_TENSOR || choice == MIDBF_CHOICE_NARROW || choice == MIDBF_CHOICE_CLUSTER ||
+           choice == MIDBF_CHOICE_GEMM;
+}
+
+// Whether a launch takes a register-tiled GEMM form (FP32 only): the middle
+// factor made on the fly with the FP32 phase (k_s_gemm), or an ID stage or
+// the stored middle factor in the row pattern (k_r_gemm) or the column
+// pattern (k_c_gemm).  Asked for (MIDBF_CHOICE_GEMM), or by default: the row
+// pattern from kGemmMinRhs RHS on; the column pattern from kGemmMinRhs RHS
+// on when its IDs have 64 redundant columns or more (the tile has 64 column
+// slots; on the 64-RHS FIO2D plan a stage of ~16 redundant columns per ID ran
+// 1.5x slower than the SIMT tiles); the middle factor made on the fly from
+// kSGemmMinRhs RHS on (at 64 RHS the 16-RHS SIMT tile, which makes every
+// entry four times, was 7% faster).
+template <class R>
+inline bool use_gemm(const DevStage<R>& ds, int nrhs, int choice, bool row_pattern) {
+    if (sizeof(R) != 4 || (!ds.id && ds.s_df)) return false;
+    if (choice == MIDBF_CHOICE_GEMM) return true;
+    if (choice != MIDBF_CHOICE_DEFAULT) return false;
+    if (!ds.id) return nrhs >= kSGemmMinRhs;
+    return nrhs >= kGemmMinRhs && (row_pattern || ds.max_nred >= 64);
 }
 
 inline int choice_tile(int choice) {
@@ -308,6 +331,12 @@ void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool c
 template <class R>
 void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, bool adjoint, cudaStream_t s,
               int force = 0, bool persist = false);
+void launch_s_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint,
+                   cudaStream_t s);
+void launch_c_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool conj,
+                   cudaStream_t s);
+void launch_r_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool conj,
+                   cudaStream_t s);
 void launch_tc(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint, bool refine,
                __nv_bfloat16* bimg, int* status, cudaStream_t s);
 void launch_blk_tc(const DevStage<float>& ds, int o, VecRef<float> src, VecRef<float> dst, int nrhs, bool refine,

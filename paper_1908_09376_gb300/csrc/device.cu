@@ -825,7 +825,8 @@ int grid_for(const void* kernel, size_t smem, int nitems, bool persist) {
 // MIDBF_CHOICE_COLUMN1 (the one-RHS pattern-C kernel), each optionally with
 // MIDBF_CHOICE_PERSIST; or one of MIDBF_CHOICE_NARROW (the narrow-ID
 // kernels), MIDBF_CHOICE_CLUSTER (the one-RHS row pattern on clusters of
-// CTAs) and MIDBF_CHOICE_TENSOR.
+// CTAs), MIDBF_CHOICE_GEMM (the FP32 middle factor as a register-tiled GEMM)
+// and MIDBF_CHOICE_TENSOR.
 template <class R>
 void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, VecRef<R> src, VecRef<R> dst, int nrhs,
                   int choice, __nv_bfloat16* bimg, cudaStream_t s) {
@@ -855,8 +856,19 @@ void launch_stage(const midbf_dplan* dp, const DevStage<R>& ds, bool adjoint, Ve
         } else if (narrow) {
             if (use_r) launch_r_narrow<R>(ds, src, dst, adjoint, s);
             else launch_c_narrow<R>(ds, src, dst, adjoint, s);
-        } else if (use_r) launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
-        else launch_c<R>(ds, src, dst, nrhs, adjoint, s, col1 ? MIDBF_CHOICE_COLUMN1 : tile, persist);
+        } else if (use_gemm(ds, nrhs, choice, use_r)) {
+            if constexpr (sizeof(R) == 4) {
+                if (use_r) launch_r_gemm(ds, src, dst, nrhs, adjoint, s);
+                else launch_c_gemm(ds, src, dst, nrhs, adjoint, s);
+            }
+        } else if (use_r) {
+            launch_r<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
+        } else {
+            launch_c<R>(ds, src, dst, nrhs, adjoint, s, col1 ? MIDBF_CHOICE_COLUMN1 : tile, persist);
+        }
+    } else if constexpr (sizeof(R) == 4) {
+        if (use_gemm(ds, nrhs, choice, false)) launch_s_gemm(ds, src, dst, nrhs, adjoint, s);
+        else launch_s<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
     } else {
         launch_s<R>(ds, src, dst, nrhs, adjoint, s, tile, persist);
     }
@@ -1018,6 +1030,7 @@ std::vector<int> stage_candidates(const midbf_dplan* dp, const DevStage<R>& ds, 
         (use_r || pattern_c_smem<R>(ds.max_narrow, ds.max_nsub, kRangeC1, 1) <= kSmemCap))
         c.push_back(MIDBF_CHOICE_NARROW);
     if (ds.id && use_r && nrhs == 1) c.push_back(MIDBF_CHOICE_CLUSTER);
+    if (sizeof(R) == 4 && (ds.id || !ds.s_df) && nrhs >= 8) c.push_back(MIDBF_CHOICE_GEMM);
     if (sizeof(R) == 4 && (ds.id ? ds.tc : dp->tc_mode != 0)) c.push_back(MIDBF_CHOICE_TENSOR);
     return c;
 }

@@ -172,6 +172,32 @@ void launch_c_narrow(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, bool c
     CK(cudaGetLastError());
 }
 
+// Many RHS in FP32: the column pattern as a register-tiled GEMM (k_c_gemm)
+// over the pattern-C items.
+void launch_c_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool conj,
+                   cudaStream_t s) {
+    if (ds.n_items_c == 0) return;
+    const size_t sm = c_gemm_smem();
+    auto kf = conj ? k_c_gemm<true> : k_c_gemm<false>;
+    set_smem(kf, sm);
+    kf<<<ds.n_items_c, kThreads, sm, s>>>(ds.ids, src, dst, nrhs);
+    CK(cudaGetLastError());
+}
+
+// Many RHS in FP32: the row pattern as a register-tiled GEMM (k_r_gemm) over
+// the row items (32 or 64 rows each).
+void launch_r_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool conj,
+                   cudaStream_t s) {
+    if (ds.n_items_r == 0) return;
+    const int rows = 32 * ds.rt;
+    if (rows > kRgRows) fail(MIDBF_EINTERNAL, "row items larger than the row GEMM tile");
+    const size_t sm = r_gemm_smem();
+    auto kf = conj ? k_r_gemm<true> : k_r_gemm<false>;
+    set_smem(kf, sm);
+    kf<<<ds.n_items_r, kThreads, sm, s>>>(ds.ids, src, dst, nrhs, rows);
+    CK(cudaGetLastError());
+}
+
 template void launch_r_narrow<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, cudaStream_t);
 template void launch_r_narrow<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, bool, cudaStream_t);
 template void launch_c_narrow<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, bool, cudaStream_t);

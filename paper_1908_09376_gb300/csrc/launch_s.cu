@@ -121,6 +121,41 @@ void launch_s(const DevStage<R>& ds, VecRef<R> src, VecRef<R> dst, int nrhs, boo
     CK(cudaGetLastError());
 }
 
+// Many RHS in FP32: the register-tiled GEMM form of the middle factor
+// (k_s_gemm), 64-row items.
+template <bool CJ, int PQ>
+void launch_s_gemm_t(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, cudaStream_t s) {
+    SStage<float> st = ds.ss;
+    st.items = !CJ ? ds.items_rows : ds.items_cols;
+    const int n = !CJ ? ds.n_items_rows : ds.n_items_cols;
+    if (n == 0) return;
+    const size_t sm = s_gemm_smem(st.P, st.Q);
+    auto kf = k_s_gemm<CJ, PQ>;
+    set_smem(kf, sm);
+    kf<<<n, kThreads, sm, s>>>(st, !CJ ? ds.srows : ds.scols, !CJ ? ds.scols : ds.srows, !CJ ? 1 : 0, src, dst, nrhs);
+}
+
+template <bool CJ>
+void launch_s_gemm_cj(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, cudaStream_t s) {
+    switch (s_shape(ds)) {
+        case 1: launch_s_gemm_t<CJ, 1>(ds, src, dst, nrhs, s); break;
+        case 2: launch_s_gemm_t<CJ, 2>(ds, src, dst, nrhs, s); break;
+        case 3: launch_s_gemm_t<CJ, 3>(ds, src, dst, nrhs, s); break;
+        case 4: launch_s_gemm_t<CJ, 4>(ds, src, dst, nrhs, s); break;
+        case 5: launch_s_gemm_t<CJ, 5>(ds, src, dst, nrhs, s); break;
+        case kShapeDistance: launch_s_gemm_t<CJ, kShapeDistance>(ds, src, dst, nrhs, s); break;
+        default: launch_s_gemm_t<CJ, 0>(ds, src, dst, nrhs, s);
+    }
+}
+
+void launch_s_gemm(const DevStage<float>& ds, VecRef<float> src, VecRef<float> dst, int nrhs, bool adjoint,
+                   cudaStream_t s) {
+    if (ds.s_df) fail(MIDBF_EINTERNAL, "the GEMM form of the middle factor takes the FP32 phase");
+    if (adjoint) launch_s_gemm_cj<true>(ds, src, dst, nrhs, s);
+    else launch_s_gemm_cj<false>(ds, src, dst, nrhs, s);
+    CK(cudaGetLastError());
+}
+
 template void launch_s<float>(const DevStage<float>&, VecRef<float>, VecRef<float>, int, bool, cudaStream_t, int, bool);
 template void launch_s<double>(const DevStage<double>&, VecRef<double>, VecRef<double>, int, bool, cudaStream_t, int, bool);
 

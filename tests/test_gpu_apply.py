@@ -306,3 +306,36 @@ def test_cluster_row_kernel_matches_oracle(case, prec, s_mode):
         _check(g3[:, r], midbf.apply(fac, f[:, r], mats), TOL[prec], f"{case} 3 RHS forward")
         _check(a3[:, r], midbf.apply_adjoint(fac, y[:, r], mats), TOL[prec], f"{case} 3 RHS adjoint")
     assert dp.status() == mb.OK
+
+
+@pytest.mark.parametrize("case", ["fio2d_n64_L3", "jump_n32_L2", "fio3d_n8_L2", "lowrank_n32_L3", "dot_n16_L2"])
+@pytest.mark.parametrize("s_mode", [mb.S_ONTHEFLY, mb.S_STORED])
+def test_gemm_forms_match_oracle(case, s_mode):
+    """The FP32 register-tiled complex GEMM forms (4 x 4 micro-tiles per
+    thread, RHS in tiles of 64): the middle factor made on the fly (k_s_gemm:
+    64 x 32 tiles of S made once in shared memory), and the row and column
+    patterns of the V/U stages and of the stored middle factor (k_r_gemm,
+    k_c_gemm: T copied by 16-byte cp.async into shared memory).  Forced on every stage for 1,
+    5 and 70 RHS (a ragged second RHS tile), and under the default rules at
+    40 RHS (the ID stages' GEMM forms), forward and adjoint, against the
+    oracle's apply of the same factors; a batched call with a 40-RHS instance
+    equals the single apply bit for bit."""
+    fac, plan, mats = oracle_case(case)
+    dp = mb.DevicePlan(plan, mb.FP32, s_mode)
+    for nrhs in (1, 5, 70):
+        for q in range(len(dp.stage_info())):
+            for adj in (0, 1):
+                dp.set_choice(nrhs, q, adj, mb.CHOICE_GEMM)
+    for nrhs in (1, 5, 40, 70):
+        f = synth.complex_gaussian(fac.nw, nrhs, 70 + nrhs)
+        h = synth.complex_gaussian(fac.nx, nrhs, 71 + nrhs)
+        g = dp.apply(torch.from_numpy(f.T.copy()).to("cuda", torch.complex64)).cpu().numpy().T
+        a = dp.apply(torch.from_numpy(h.T.copy()).to("cuda", torch.complex64), adjoint=True).cpu().numpy().T
+        for r in range(0, nrhs, max(1, nrhs // 4)):
+            _check(g[:, r], midbf.apply(fac, f[:, r], mats), TOL[mb.FP32], f"{case} gemm forward {nrhs}/{r}")
+            _check(a[:, r], midbf.apply_adjoint(fac, h[:, r], mats), TOL[mb.FP32], f"{case} gemm adjoint {nrhs}/{r}")
+    x = torch.from_numpy(synth.complex_gaussian(fac.nw, 40, 90).T.copy()).to("cuda", torch.complex64)
+    y = torch.from_numpy(synth.complex_gaussian(fac.nx, 3, 91).T.copy()).to("cuda", torch.complex64)
+    outs = mb.apply_batched([dp, dp], [x, y], [0, 1])
+    assert torch.equal(outs[0], dp.apply(x)) and torch.equal(outs[1], dp.apply(y, adjoint=True))
+    assert dp.status() == mb.OK

@@ -3,7 +3,8 @@
 Every stage of an apply can run several kernel variants (SIMT RHS tiles, the
 one-RHS column kernel, each of them one CTA per item or persistent, the
 narrow-ID kernels for one RHS and low ranks, the one-RHS row pattern on
-thread-block clusters, and the tensor-core kernels).  Forcing each variant of
+thread-block clusters, the FP32 middle factor as a register-tiled GEMM, and
+the tensor-core kernels).  Forcing each variant of
 each stage in turn must reproduce the oracle's FP64 apply of the same
 factors (FP32: 2e-5; tensor cores with refinement: 2e-5; tolerances as in
 test_gpu_apply / test_gpu_tensor), and the autotuner must record, for every
@@ -42,7 +43,7 @@ def _ref(fac, mats, f, adjoint):
 @pytest.mark.parametrize("mode,nrhs,choices", [
     (mb.FP32, 1, [1, mb.CHOICE_COLUMN1, 1 | mb.CHOICE_PERSIST, mb.CHOICE_COLUMN1 | mb.CHOICE_PERSIST]),
     (mb.FP32, 1, [mb.CHOICE_NARROW, mb.CHOICE_CLUSTER]),
-    (mb.FP32, 20, [1, 2, 4, 8, 16, 16 | mb.CHOICE_PERSIST]),
+    (mb.FP32, 20, [1, 2, 4, 8, 16, 16 | mb.CHOICE_PERSIST, mb.CHOICE_GEMM]),
     (mb.BF16 | mb.REFINE, 20, [4, 16 | mb.CHOICE_PERSIST, mb.CHOICE_TENSOR]),
 ])
 def test_every_forced_variant_matches_oracle(mode, nrhs, choices):
@@ -86,6 +87,9 @@ def test_autotune_records_valid_choices_and_keeps_results(mode, nrhs):
                 continue
             if ch in (mb.CHOICE_NARROW, mb.CHOICE_CLUSTER):   # narrow-ID or cluster kernels: one RHS
                 assert nrhs == 1
+                continue
+            if ch == mb.CHOICE_GEMM:   # the register-tiled FP32 GEMM forms (FP32 data: FP32 and BF16 plans)
+                assert mode != mb.FP64 and nrhs >= 8
                 continue
             base = ch & ~mb.CHOICE_PERSIST
             assert base in simt, (stage, adj, ch)
