@@ -406,9 +406,12 @@ void midbf_graph_destroy(midbf_graph* graph);
 /* ---- kernel choices and the autotuner ------------------------------------
  * Every stage of an apply runs one kernel variant.  By default the library
  * picks it by fixed rules: the tensor-core kernels in the MIDBF_BF16 modes
- * from 16 RHS on, else the SIMT kernel with the smallest RHS tile that covers
- * nrhs (at most 16 in FP32, 8 in FP64) and fits shared memory, one CTA per
- * work item.  A choice per (nrhs, stage, direction) overrides the rules:
+ * from 16 RHS on; in FP32 the GEMM forms (MIDBF_CHOICE_GEMM) from 32 RHS on
+ * as described beside that constant; for one RHS the narrow-ID and cluster
+ * kernels as described beside theirs; else the SIMT kernel with the smallest
+ * RHS tile that covers nrhs (at most 16 in FP32, 8 in FP64) and fits shared
+ * memory, one CTA per work item.  A choice per (nrhs, stage, direction)
+ * overrides the rules:
  *   MIDBF_CHOICE_DEFAULT  the rules;
  *   1, 2, 4, 8, 16        the SIMT kernel with this RHS tile (taken when it
  *                         fits shared memory; else the rules' tile);
@@ -419,11 +422,14 @@ void midbf_graph_destroy(midbf_graph* graph);
  *                         CTAs as are resident on the GPU at once, each
  *                         looping over the level's work items;
  *   MIDBF_CHOICE_TENSOR   the tensor-core kernel (BF16 modes only; else the
- *                         rules).
+ *                         rules);
+ *   MIDBF_CHOICE_NARROW, MIDBF_CHOICE_CLUSTER, MIDBF_CHOICE_GEMM
+ *                         below (each falls back to the rules where it does
+ *                         not apply).
  * midbf_autotune times every applicable variant of every stage in both
  * directions for nrhs right-hand sides on `stream` and records the fastest;
- * later applies with that nrhs use it (midbf_apply_batched uses the SIMT
- * tiles).  It allocates and frees temporary device vectors, waits for the
+ * later applies with that nrhs use it (midbf_apply_batched uses the tuned
+ * choices too, launching the narrow, cluster and GEMM ones per instance).  It allocates and frees temporary device vectors, waits for the
  * stream, and must not run concurrently with applies of the same dplan or
  * while the stream records a graph.  midbf_set_choice records a choice by
  * hand, midbf_get_choice reads the one in force.  stage: index in forward
